@@ -1,0 +1,43 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def load_blocks(name):
+    """Parse a golden table file made of '[Name]' blocks of 'i: v1 v2 ...' lines."""
+    blocks, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for ln in fh:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            if ln.startswith("["):
+                cur = ln[1:-1]
+                blocks[cur] = {}
+                continue
+            r, vals = ln.split(":")
+            blocks[cur][int(r)] = [int(v) for v in vals.split()]
+    return blocks
+
+
+def load_rows(name):
+    """Parse a golden file of whitespace-separated integer rows."""
+    out = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for ln in fh:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                out.append([int(v) for v in ln.split()])
+    return out

@@ -1,0 +1,321 @@
+"""Pins of the oracle's integer side against what the paper prints and proves.
+
+Every expected number here is either printed in the paper (fixtures under
+tests/golden/, each citing its table) or a closed form stated in the paper
+(Theorem 1, Propositions 1 and 2, the weight invariant of Section 2.2, the
+coarse-grain critical paths of Section 3.1).
+"""
+
+import itertools
+import math
+
+import pytest
+
+from conftest import load_blocks, load_rows
+from oracle import (BINARY, FIBONACCI, FLAT_TS, FLAT_TT, GREEDY, PLASMA,
+                    SAMEH_KUCK)
+from oracle import dag, trees
+
+TILED = {"FlatTree": (FLAT_TT, 1), "Fibonacci": (FIBONACCI, 1), "Greedy": (GREEDY, 1),
+         "BinaryTree": (BINARY, 1), "PlasmaTree5": (PLASMA, 5)}
+
+
+def zero_table(p, q, tree, BS=1, ts=False):
+    el = trees.elimination_list(p, q, tree, BS)
+    tasks = dag.expand(p, q, el, ts)
+    fin, cp = dag.simulate(tasks)
+    return dag.zero_times(tasks, fin), cp
+
+
+@pytest.mark.parametrize("name", sorted(TILED))
+def test_tiled_zero_times_15x6(name):
+    """Table tab.tiled (Section 3.2): every zero-out time of five trees."""
+    gold = load_blocks("tab_tiled_15x6.txt")[name]
+    tree, BS = TILED[name]
+    zt, _ = zero_table(15, 6, tree, BS)
+    for i, vals in gold.items():
+        for k, v in enumerate(vals, start=1):
+            assert zt[(i, k)] == v, (name, i, k)
+
+
+def test_coarse_times_15x6():
+    """Table tab.coarse (Section 3.1): Sameh-Kuck, Fibonacci and Greedy."""
+    gold = load_blocks("tab_coarse_15x6.txt")
+    got = {
+        "SamehKuck": trees.coarse_asap(15, 6, trees.sameh_kuck(15, 6)),
+        "Fibonacci": trees.coarse_fibonacci(15, 6),
+        "Greedy": trees.coarse_greedy(15, 6),
+    }
+    for name, table in gold.items():
+        for i, vals in table.items():
+            for k, v in enumerate(vals, start=1):
+                assert got[name][(i, k)] == v, (name, i, k)
+
+
+def test_greedy_15x3():
+    """Table table.15x2x3 (a): Greedy on 15x3 (first two columns = 15x2 case)."""
+    gold = load_blocks("tab_15x2x3.txt")["Greedy"]
+    zt, cp = zero_table(15, 3, GREEDY)
+    for i, vals in gold.items():
+        for k, v in enumerate(vals, start=1):
+            assert zt[(i, k)] == v, (i, k)
+    assert cp == 64          # Section 3.2: Greedy finishes at time-step 64
+    zt2, _ = zero_table(15, 2, GREEDY)
+    for i, vals in gold.items():
+        for k, v in enumerate(vals[:2], start=1):
+            assert zt2[(i, k)] == v
+
+
+def test_greedy_biggermat():
+    """Table table.biggermat: Greedy critical paths, p, q in {16..128}, q <= 64."""
+    for p, q, g, _asap in load_rows("biggermat_cp.txt"):
+        if q > 64:
+            continue                      # 128x128 is covered by the slow sweep below
+        assert dag.critical_path(p, q, trees.greedy(p, q)) == g, (p, q)
+
+
+def test_greedy_biggermat_128x128():
+    p, q, g, _ = [r for r in load_rows("biggermat_cp.txt") if r[1] == 128][0]
+    assert dag.critical_path(p, q, trees.greedy(p, q)) == g
+
+
+def test_p40_greedy_fibonacci_plasma_printed_bs():
+    """Section 4 theoretical table, p = 40, q = 1..40: Greedy and Fibonacci CPs,
+    and PlasmaTree's CP at the printed best domain size."""
+    for p, q, g, pt, bs, fib in load_rows("p40_cp.txt"):
+        assert dag.critical_path(p, q, trees.greedy(p, q)) == g, q
+        assert dag.critical_path(p, q, trees.fibonacci(p, q)) == fib, q
+        assert dag.critical_path(p, q, trees.plasma_tree(p, q, bs)) == pt, q
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 6, 11, 21, 40])
+def test_p40_plasma_best_bs(q):
+    """The printed BS is the smallest domain size reaching the minimum CP."""
+    row = [r for r in load_rows("p40_cp.txt") if r[1] == q][0]
+    p, _, _, pt, bs, _ = row
+    cps = [dag.critical_path(p, q, trees.plasma_tree(p, q, b)) for b in range(1, p + 1)]
+    assert min(cps) == pt
+    assert cps.index(pt) + 1 == bs
+
+
+# ---------------------------------------------------------------- closed forms
+def flat_tt_cp(p, q):
+    if q == 1:
+        return 2 * p + 2
+    if p > q:
+        return 6 * p + 16 * q - 22
+    return 22 * p - 24
+
+
+def flat_ts_cp(p, q):
+    if q == 1:
+        return 6 * p - 2
+    if p > q:
+        return 12 * p + 18 * q - 32
+    return 30 * p - 34
+
+
+@pytest.mark.parametrize("p", range(2, 21))
+def test_theorem1_flat_tree(p):
+    """Theorem 1 (1): CP of FlatTree is 2p+2, 6p+16q-22 or 22p-24."""
+    for q in range(1, p + 1):
+        assert dag.critical_path(p, q, trees.sameh_kuck(p, q)) == flat_tt_cp(p, q), (p, q)
+
+
+@pytest.mark.parametrize("p", range(2, 21))
+def test_proposition2_flat_tree_ts(p):
+    """Proposition 2: CP of TS-FlatTree is 6p-2, 12p+18q-32 or 30p-34."""
+    for q in range(1, p + 1):
+        assert dag.critical_path(p, q, trees.sameh_kuck(p, q), ts=True) == flat_ts_cp(p, q), (p, q)
+
+
+def test_proposition1_binary_tree():
+    """Proposition 1: (10 + 6 log2 p) q - 4 log2 p - 6 for powers of two, q < p."""
+    for lp in range(1, 7):
+        p = 2 ** lp
+        for lq in range(0, lp):
+            q = 2 ** lq
+            want = (10 + 6 * lp) * q - 4 * lp - 6
+            assert dag.critical_path(p, q, trees.binary_tree(p, q)) == want, (p, q)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 8, 13, 17, 24, 33, 40])
+def test_theorem1_upper_bounds(p):
+    """Theorem 1 (2): Fibonacci <= 22q + 6 ceil(sqrt(2p)), Greedy <= 22q + 6 ceil(log2 p)."""
+    for q in range(1, p + 1):
+        assert dag.critical_path(p, q, trees.fibonacci(p, q)) <= 22 * q + 6 * math.ceil(math.sqrt(2 * p))
+        assert dag.critical_path(p, q, trees.greedy(p, q)) <= 22 * q + 6 * math.ceil(math.log2(p))
+
+
+def test_coarse_closed_forms():
+    """Section 3.1: coarse CP of Sameh-Kuck is p+q-2 (p>q), 2q-3 (square);
+    Fibonacci is x+2q-2 (p>q), x+2q-4 (square)."""
+    for p in range(2, 30):
+        for q in range(1, p + 1):
+            sk = max(trees.coarse_asap(p, q, trees.sameh_kuck(p, q)).values())
+            fib = max(trees.coarse_fibonacci(p, q).values())
+            x = trees.fibonacci_x(p)
+            if p > q:
+                assert sk == p + q - 2 and fib == x + 2 * q - 2, (p, q)
+            elif q > 1:
+                assert sk == 2 * q - 3 and fib == x + 2 * q - 4, (p, q)
+
+
+# ------------------------------------------------------------------ invariants
+ALL = [(FLAT_TS, 1, True), (FLAT_TT, 1, False), (SAMEH_KUCK, 1, False), (BINARY, 1, False),
+       (FIBONACCI, 1, False), (GREEDY, 1, False), (PLASMA, 3, False)]
+
+
+@pytest.mark.parametrize("tree,BS,ts", ALL)
+def test_total_weight_and_validity(tree, BS, ts):
+    """Section 2.2: any valid list weighs 6pq^2 - 2q^3; generated lists are valid
+    and have no reverse elimination (Lemma 1 form)."""
+    for p in range(1, 14):
+        for q in range(1, p + 1):
+            el = trees.elimination_list(p, q, tree, BS)
+            assert trees.validate(p, q, el) is None, (p, q)
+            assert all(piv < i for (i, piv, k) in el)
+            assert len(el) == sum(p - k for k in range(1, q + 1))
+            w = dag.total_weight(dag.expand(p, q, el, ts))
+            assert w == 6 * p * q * q - 2 * q ** 3, (p, q)
+
+
+def test_sameh_kuck_is_flat_tree():
+    assert trees.elimination_list(9, 4, SAMEH_KUCK) == trees.elimination_list(9, 4, FLAT_TT)
+
+
+def test_plasma_extremes():
+    """BS = p is a flat tree; BS = 1 at q = 1 has BinaryTree's critical path."""
+    for p in range(2, 20):
+        for q in range(1, p + 1):
+            assert trees.plasma_tree(p, q, p) == trees.sameh_kuck(p, q)
+        assert (dag.critical_path(p, 1, trees.plasma_tree(p, 1, 1))
+                == dag.critical_path(p, 1, trees.binary_tree(p, 1)))
+
+
+def test_example_list_of_section2():
+    """Section 2 gives, for p = 6, a valid first column other than the flat one."""
+    col1 = [(3, 1, 1), (6, 4, 1), (2, 1, 1), (5, 4, 1), (4, 1, 1)]
+    assert trees.validate(6, 1, col1) is None
+
+
+def test_validator_rejects_each_rule():
+    p, q = 5, 2
+    good = trees.greedy(p, q)
+    assert trees.validate(p, q, good) is None
+    assert trees.validate(p, q, good[:-1]) is not None                     # tile never zeroed
+    assert trees.validate(p, q, good + [good[0]]) is not None              # zeroed twice
+    # row not ready: move the first column-2 elimination before column 1's
+    c2 = [e for e in good if e[2] == 2]
+    c1 = [e for e in good if e[2] == 1]
+    assert trees.validate(p, q, [c2[0]] + c1 + c2[1:]) is not None
+    # pivot already zeroed: flat column 1 but row 2 zeroed before it pivots row 3
+    bad = [(2, 1, 1), (3, 2, 1), (4, 1, 1), (5, 1, 1)]
+    assert trees.validate(5, 1, bad) is not None
+    assert trees.validate(5, 1, [(3, 2, 1), (2, 1, 1), (4, 1, 1), (5, 1, 1)]) is None
+    assert trees.validate(p, q, [(1, 2, 1)] + good[1:]) is not None        # above the diagonal
+
+
+def test_dag_counts_16x4_greedy():
+    """Task counts of the TT expansion for a 16x4 tile matrix follow from
+    Algorithm 3 and the 'already triangle' rule: one GEQRT per tile (i,k),
+    i >= k; one TTQRT per eliminated tile; updates for every j > k."""
+    p, q = 16, 4
+    tasks = dag.expand(p, q, trees.greedy(p, q))
+    kinds = [t[0] for t in tasks]
+    assert kinds.count(dag.GEQRT) == sum(p - k + 1 for k in range(1, q + 1))
+    assert kinds.count(dag.UNMQR) == sum((p - k + 1) * (q - k) for k in range(1, q + 1))
+    assert kinds.count(dag.TTQRT) == sum(p - k for k in range(1, q + 1))
+    assert kinds.count(dag.TTMQR) == sum((p - k) * (q - k) for k in range(1, q + 1))
+    assert len(tasks) == 290
+
+
+def _all_valid_lists(p, q):
+    """Every valid elimination list without reverse eliminations, p x q tiles
+    (brute force, tiny sizes only)."""
+    cells = [(i, k) for k in range(1, q + 1) for i in range(k + 1, p + 1)]
+    out = []
+
+    def rec(prefix, zeroed):
+        if len(prefix) == len(cells):
+            out.append(list(prefix))
+            return
+        for (i, k) in cells:
+            if (i, k) in zeroed:
+                continue
+            if any((i, kp) not in zeroed for kp in range(1, k)):
+                continue
+            for piv in range(k, i):
+                if (piv, k) in zeroed or any((piv, kp) not in zeroed for kp in range(1, k)):
+                    continue
+                prefix.append((i, piv, k))
+                zeroed.add((i, k))
+                rec(prefix, zeroed)
+                zeroed.discard((i, k))
+                prefix.pop()
+
+    rec([], set())
+    return out
+
+
+def test_brute_force_optimum_tiny():
+    """Exhaustive search over valid lists on tiny matrices: the optimum is
+    never above any tree, and every enumerated list keeps the weight invariant."""
+    for p, q in [(3, 1), (3, 2), (4, 1), (4, 2), (3, 3)]:
+        lists = _all_valid_lists(p, q)
+        assert lists
+        best = min(dag.critical_path(p, q, el) for el in lists)
+        for tree in (FLAT_TT, BINARY, FIBONACCI, GREEDY, PLASMA):
+            assert best <= dag.critical_path(p, q, trees.elimination_list(p, q, tree, 2))
+        for el in lists[:50]:
+            assert trees.validate(p, q, el) is None
+            assert dag.total_weight(dag.expand(p, q, el)) == 6 * p * q * q - 2 * q ** 3
+        # Section 3.1: coarse-grain Greedy is optimal in the coarse model.
+        coarse_best = min(max(trees.coarse_asap(p, q, el).values()) for el in lists)
+        assert max(trees.coarse_greedy(p, q).values()) == coarse_best
+
+
+# ---------------------------------------------------------- planted mistakes
+def _tiled_matches(name):
+    gold = load_blocks("tab_tiled_15x6.txt")[name]
+    tree, BS = TILED[name]
+    zt, _ = zero_table(15, 6, tree, BS)
+    return all(zt[(i, k)] == v for i, vals in gold.items() for k, v in enumerate(vals, start=1))
+
+
+def test_integer_pins_catch_planted_mistakes(monkeypatch):
+    """Plausible slips in the oracle's integer side break a printed table."""
+    assert _tiled_matches("Greedy")
+    # a wrong kernel weight
+    monkeypatch.setitem(dag.WEIGHT, dag.TTQRT, 3)
+    assert not _tiled_matches("FlatTree")
+    monkeypatch.setitem(dag.WEIGHT, dag.TTQRT, 2)
+    # write-after-read edges on V (the NODEP reading dropped)
+    real = dag.dependencies
+
+    def with_war(tasks):
+        preds = real(tasks)
+        last_reader = {}
+        for t, (kind, i, piv, k, j) in enumerate(tasks):
+            if kind in (dag.UNMQR,):
+                last_reader[(i, k)] = t
+            if kind in (dag.TTQRT,) and (i, k) in last_reader:
+                preds[t] = sorted(set(preds[t]) | {last_reader[(i, k)]})
+        return preds
+
+    monkeypatch.setattr(dag, "dependencies", with_war)
+    assert not _tiled_matches("Greedy")
+    monkeypatch.setattr(dag, "dependencies", real)
+    # Fibonacci paired with column 1's block size instead of the column's own
+    real_fib = trees.fibonacci
+
+    def fib_col1_z(p, q):
+        out = []
+        for k in range(1, min(p, q) + 1):
+            for (i, piv, kk) in real_fib(p, 1):
+                if i + k - 1 <= p:
+                    out.append((i + k - 1, piv + k - 1, k))
+        return sorted(out, key=lambda e: (e[2], trees.fibonacci_coarse(p, e[0], e[2]), e[0]))
+
+    monkeypatch.setattr(trees, "fibonacci", fib_col1_z)
+    assert not _tiled_matches("Fibonacci")
