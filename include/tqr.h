@@ -1,0 +1,198 @@
+/*
+ * tqr.h -- C ABI of libtqr, tiled Householder QR factorization on one GPU.
+ *
+ * Method: Bouwmeester, Jacquelin, Langou, Robert, "Tiled QR factorization
+ * algorithms" (2011).  An m x n matrix (m >= n) is split into p x q tiles of
+ * nb x nb.  An elimination tree produces an elimination list (Section 2,
+ * Algorithm 1; validity rules of Section 2.2); each elimination expands into
+ * TS or TT kernel tasks (Algorithms 2 and 3); the tasks run as soon as their
+ * dependencies are met (Section 2.3).  The six kernels (Table 1) are GEQRT,
+ * UNMQR, TSQRT, TSMQR, TTQRT and TTMQR, with inner blocking ib.
+ *
+ * Conventions for every entry point:
+ *  - Return value: 0 (TQR_OK) on success.  A negative value -k in -1..-99
+ *    means that argument k (1-based) is invalid.  Named codes below.
+ *  - No C++ exception crosses this boundary.
+ *  - Matrices are column-major FP64.  "device" pointers are CUDA global
+ *    memory of the current device; "host" pointers are ordinary host memory.
+ *  - Device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) and returns before it completes.  Errors detected on the
+ *    device (timeout, non-finite values) surface at tqr_sync().
+ *  - Tile indices in integer outputs are 0-based: the paper's elim(i, piv, k)
+ *    with 1-based rows and columns appears as (i-1, piv-1, k-1).
+ *  - Ownership: the caller owns every matrix it passes.  The library owns
+ *    what a tqr_factors handle holds (reflector scalars, task graph,
+ *    counters) until tqr_free().
+ */
+#ifndef TQR_H
+#define TQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Elimination trees (Section 3).  TQR_FLAT_TS runs FlatTree with TS kernels
+ * (Proposition 2); every other tree runs TT kernels. */
+typedef enum {
+    TQR_FLAT_TS = 0,     /* Sameh-Kuck list, TS kernels                    */
+    TQR_FLAT_TT = 1,     /* Sameh-Kuck list, TT kernels (FlatTree)         */
+    TQR_SAMEH_KUCK = 2,  /* same list and kernels as TQR_FLAT_TT           */
+    TQR_BINARY = 3,      /* binary reduction per column (Proposition 1)    */
+    TQR_FIBONACCI = 4,   /* Fibonacci scheme of order 1 (Section 3.1)      */
+    TQR_GREEDY = 5,      /* Greedy for tiles (Algorithm 4)                 */
+    TQR_PLASMA = 6       /* PlasmaTree with domain size BS (Section 3.2)   */
+} tqr_tree;
+
+/* Kernel kinds, as reported by tqr_tasks(). */
+typedef enum {
+    TQR_GEQRT = 0, TQR_UNMQR = 1, TQR_TTQRT = 2, TQR_TTMQR = 3, TQR_TSQRT = 4, TQR_TSMQR = 5
+} tqr_kernel;
+
+#define TQR_OK 0
+#define TQR_ERR_INVALID_LIST (-100) /* elimination list breaks a Section 2.2 rule */
+#define TQR_ERR_TIMEOUT (-101)      /* a device wait ran past its time limit      */
+#define TQR_ERR_NONFINITE (-102)    /* a Householder norm was Inf or NaN          */
+#define TQR_ERR_CUDA (-103)         /* a CUDA runtime call failed                 */
+#define TQR_ERR_NOMEM (-104)        /* device or host allocation failed           */
+#define TQR_ERR_CAPACITY (-105)     /* caller's output array too small            */
+#define TQR_ERR_INTERNAL (-106)     /* inconsistent internal state                */
+#define TQR_ERR_UNSUPPORTED (-107)  /* parameters outside what the kernels handle */
+
+typedef struct tqr_factors tqr_factors;
+
+/* Summary of a factorization handle. */
+typedef struct {
+    int64_t m, n;          /* matrix size                                  */
+    int32_t nb, ib;        /* tile size and inner blocking                 */
+    int32_t p, q;          /* tile rows ceil(m/nb), tile columns ceil(n/nb) */
+    int32_t tree, BS;      /* tree (-1 for a caller-given list), domain size */
+    int32_t ts;            /* 1 if TS kernels, 0 if TT                     */
+    int32_t strip;         /* columns per update task on the device        */
+    int64_t n_elims;       /* length of the elimination list               */
+    int64_t n_tile_tasks;  /* kernel tasks (Algorithms 2/3)                */
+    int64_t n_device_tasks;/* tasks after splitting updates into strips    */
+    int64_t n_edges;       /* dependency edges of the device task graph    */
+    int64_t critical_path; /* unit-weight critical path, units of nb^3/3    */
+    double flops;          /* 2 n^2 (m - n/3), the LAPACK count (Section 2.2) */
+} tqr_info;
+
+/* ---------------------------------------------------------------------------
+ * Factorization (Sections 2.1-2.3).
+ *
+ * tqr_factor: A = Q R in place.  A is a device pointer to an m x n matrix,
+ * column-major, leading dimension m (lda = m), m >= n >= 1.  On return (once
+ * the stream reaches it) A holds R in its upper triangle and the Householder
+ * reflectors V below it and in the zeroed tiles, exactly as LAPACK/PLASMA's
+ * GEQRT, TTQRT and TSQRT leave them; the reflectors' tau values stay inside
+ * the handle.  m and n need not be multiples of nb: the last tile row/column
+ * is ragged and behaves as if zero-padded (R and V are unchanged by the
+ * padding).
+ *   nb:   tile size, 8 <= nb <= 256, nb % 4 == 0.
+ *   ib:   inner blocking, ib divides nb, ib <= 64.
+ *   tree: a tqr_tree value.  BS: PlasmaTree domain size, 1 <= BS <= p
+ *         (ignored by other trees).
+ *   out:  receives the handle.  If *out already holds a handle made for the
+ *         same (m, n, nb, ib, tree, BS), its device buffers are reused and
+ *         nothing is allocated; otherwise a new handle is created (the old
+ *         one is left untouched).  Set *out = NULL before the first call.
+ * Errors: -1..-9 argument errors, TQR_ERR_NOMEM, TQR_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
+               void* stream, tqr_factors** out);
+
+/* Same with a caller-given elimination list: `list` (host) holds `count`
+ * 0-based triplets (i, piv, k) in order; ts = 1 selects TS kernels, 0 TT.
+ * The list is checked against the rules of Section 2.2 first
+ * (TQR_ERR_INVALID_LIST).  *out is reused only if it was made from the same
+ * list. */
+int tqr_factor_list(double* A, int64_t m, int64_t n, int nb, int ib, const int32_t* list,
+                    int64_t count, int ts, void* stream, tqr_factors** out);
+
+/* B <- Q^T B (tqr_apply_qt) or B <- Q B (tqr_apply_q) with the Q of a
+ * factorization.  B: device, m x nrhs, column-major, leading dimension
+ * ldb >= m.  The transformations are replayed in elimination-list order (or
+ * reverse order for Q), on the stream given.  The factorization must have been
+ * enqueued earlier on the same stream (or be complete). */
+int tqr_apply_qt(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stream);
+int tqr_apply_q(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stream);
+
+/* Compact-WY T factors (Section 1; LAPACK/PLASMA storage) of every GEQRT
+ * and of every TTQRT/TSQRT, formed from the stored reflectors.  Each output
+ * is a device array of p*q tiles of ib x nb doubles; the T of tile (i,k)
+ * (0-based) starts at offset ((size_t)k*p + i)*ib*nb and is column-major
+ * ib x nb: columns b*ib..b*ib+ib-1 hold the upper-triangular ib x ib factor
+ * of reflectors b*ib..b*ib+ib-1.  T_geqrt receives the T of GEQRT(i,k);
+ * T_elim the T of the TTQRT/TSQRT that zeroed tile (i,k).  Tiles without
+ * such a kernel are set to zero.  Either pointer may be NULL. */
+int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream);
+
+/* Waits for the handle's last enqueued work and returns its device status:
+ * TQR_OK, TQR_ERR_TIMEOUT, TQR_ERR_NONFINITE or TQR_ERR_CUDA. */
+int tqr_sync(tqr_factors* f);
+
+/* Fills *info.  Host only. */
+int tqr_get_info(const tqr_factors* f, tqr_info* info);
+
+/* Releases the handle's device and host memory (synchronizes first). */
+void tqr_free(tqr_factors* f);
+
+/* End-to-end convenience for host data: copies A_host (m x n, column-major,
+ * leading dimension m) to the device, factors it, and copies A (R and V)
+ * back to A_host; if B_host is not NULL it also copies B_host (m x nrhs,
+ * leading dimension m) in, applies Q^T and copies it back.  Device buffers
+ * are owned by the handle and reused across calls with the same shape (set
+ * *out = NULL before the first call).  Synchronizes before returning. */
+int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
+                    double* B_host, int64_t nrhs, void* stream, tqr_factors** out);
+
+/* ---------------------------------------------------------------------------
+ * Host-only integer entry points (no GPU needed).
+ * ------------------------------------------------------------------------- */
+
+/* Elimination list of `tree` for p x q tiles (p >= q >= 1), as 0-based
+ * triplets (i, piv, k) written to out[3*e .. 3*e+2] for e < *count.
+ * cap: capacity of `out` in triplets; TQR_ERR_CAPACITY if too small (then
+ * *count holds the needed size). */
+int tqr_elimination_list(int p, int q, int tree, int BS, int32_t* out, int64_t cap,
+                         int64_t* count);
+
+/* TQR_OK if the list is a valid elimination list for p x q tiles (Section
+ * 2.2: one entry per subdiagonal tile of the first min(p,q) columns, both
+ * rows ready, pivot still a potential annihilator), else
+ * TQR_ERR_INVALID_LIST. */
+int tqr_validate_list(int p, int q, const int32_t* list, int64_t count);
+
+/* Critical path of `tree` in units of nb^3/3 flops (Table 1 weights,
+ * unbounded processors, every kernel starts as soon as its dependencies
+ * are met).  zero_time, if not NULL, receives p*q values: zero_time[i*q+k]
+ * = time at which tile (i,k) is zeroed, or -1 for tiles that are not. */
+int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero_time);
+
+/* Kernel tasks of `tree` in program order (Algorithms 2 and 3), as 5 ints
+ * per task: kind (tqr_kernel), i, piv, k, j (0-based; piv = -1 for GEQRT and
+ * UNMQR, j = -1 for the three panel kernels).  finish, if not NULL, receives
+ * each task's unit-weight ASAP finish time.  cap in tasks. */
+int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int64_t cap,
+              int64_t* count);
+
+/* Test support for failure detection (the paper has no counterpart).
+ * tqr_set_timeout_ms: limit, in milliseconds, for any single device wait of
+ * later launches (ms <= 0 restores the default, which scales with the
+ * problem's flop count; the TQR_TIMEOUT_MS environment variable also sets it).
+ * tqr_inject_fault(1): the next factorization or apply launch drops its
+ * initially ready tasks on the host, so no task ever becomes ready, every
+ * wait runs out, and tqr_sync() reports TQR_ERR_TIMEOUT; the device context
+ * stays usable.  tqr_inject_fault(0) cancels a pending injection. */
+int tqr_set_timeout_ms(double ms);
+int tqr_inject_fault(int kind);
+
+/* Message for a status code. */
+const char* tqr_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQR_H */

@@ -1,0 +1,610 @@
+// C ABI of libtqr (declared in include/tqr.h): argument checking, the cache of
+// task-graph plans, factorization handles, and the host-only integer entry
+// points.  No C++ exception crosses this boundary.
+#include "tqr_internal.h"
+#include "../../include/tqr.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+
+namespace tqr {
+
+// A task graph uploaded to the device.
+struct DevGraphOwner {
+    DevGraph d;
+    ~DevGraphOwner() {
+        cudaFree(d.tasks);
+        cudaFree(d.succ_ptr);
+        cudaFree(d.succ);
+        cudaFree(d.indeg);
+        cudaFree(d.ready);
+    }
+};
+
+template <class T>
+static cudaError_t upload(T** dst, const std::vector<T>& src) {
+    *dst = nullptr;
+    const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static cudaError_t upload_graph(const Graph& g, DevGraphOwner& o) {
+    cudaError_t e;
+    if ((e = upload(&o.d.tasks, g.tasks)) != cudaSuccess) return e;
+    if ((e = upload(&o.d.succ_ptr, g.succ_ptr)) != cudaSuccess) return e;
+    if ((e = upload(&o.d.succ, g.succ)) != cudaSuccess) return e;
+    if ((e = upload(&o.d.indeg, g.indeg)) != cudaSuccess) return e;
+    if ((e = upload(&o.d.ready, g.ready)) != cudaSuccess) return e;
+    o.d.ntasks = static_cast<int32_t>(g.tasks.size());
+    o.d.nready = static_cast<int32_t>(g.ready.size());
+    o.d.nedges = static_cast<int64_t>(g.succ.size());
+    return cudaSuccess;
+}
+
+struct PlanKey {
+    int64_t m, n;
+    int nb, ib, tree, BS, ts, device;
+    std::vector<Elim> list;   // only for caller-given lists (tree = -1)
+    bool operator<(const PlanKey& o) const {
+        auto a = std::tie(m, n, nb, ib, tree, BS, ts, device);
+        auto b = std::tie(o.m, o.n, o.nb, o.ib, o.tree, o.BS, o.ts, o.device);
+        if (a != b) return a < b;
+        if (list.size() != o.list.size()) return list.size() < o.list.size();
+        return std::memcmp(list.data(), o.list.data(), list.size() * sizeof(Elim)) < 0;
+    }
+};
+
+// Everything derived from (m, n, nb, ib, elimination list, kernel family).
+struct Plan {
+    PlanKey key;
+    int p = 0, q = 0, G = 0, W = 0, smem = 0;
+    bool ts = false;
+    std::vector<Elim> elims;
+    std::vector<TileTask> tt;
+    int64_t cp = 0;
+    Graph g;
+    DevGraphOwner dg;
+    int32_t* d_panels = nullptr;   // (kind, i, k) of every panel task
+    int npanels = 0;
+    std::mutex mu;
+    std::map<std::pair<int, int>, std::unique_ptr<DevGraphOwner>> apply;   // (nstrips, trans)
+    ~Plan() { cudaFree(d_panels); }
+};
+
+static std::mutex g_plans_mu;
+static std::map<PlanKey, std::shared_ptr<Plan>>& plans() {
+    static auto* m = new std::map<PlanKey, std::shared_ptr<Plan>>();   // lives until exit
+    return *m;
+}
+
+static double lapack_flops(int64_t m, int64_t n) {
+    const double M = static_cast<double>(m), N = static_cast<double>(n);
+    return 2.0 * N * N * (M - N / 3.0);
+}
+
+static int make_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
+    auto P = std::make_shared<Plan>();
+    P->key = key;
+    P->p = static_cast<int>((key.m + key.nb - 1) / key.nb);
+    P->q = static_cast<int>((key.n + key.nb - 1) / key.nb);
+    P->ts = key.ts != 0;
+    if (key.tree >= 0) {
+        int rc = make_elims(P->p, P->q, key.tree, key.BS, P->elims);
+        if (rc != TQR_OK) return rc;
+    } else {
+        P->elims = key.list;
+    }
+    if (validate_elims(P->p, P->q, P->elims.data(), static_cast<int64_t>(P->elims.size())) != TQR_OK)
+        return TQR_ERR_INVALID_LIST;
+    expand_tasks(P->p, P->q, P->elims, P->ts, P->tt);
+    P->cp = simulate(P->p, P->q, P->tt, nullptr);
+    if (!choose_layout(key.nb, key.ib, &P->G, &P->smem)) return TQR_ERR_UNSUPPORTED;
+    P->W = strip_width(P->G);
+    const int last_cols = static_cast<int>(key.n - static_cast<int64_t>(P->q - 1) * key.nb);
+    build_factor_graph(P->p, P->q, key.nb, P->W, last_cols, P->tt, P->g);
+    if (upload_graph(P->g, P->dg) != cudaSuccess) return TQR_ERR_CUDA;
+    std::vector<int32_t> panels;
+    for (const TileTask& x : P->tt)
+        if (x.kind == GEQRT || x.kind == TTQRT || x.kind == TSQRT) {
+            panels.push_back(x.kind);
+            panels.push_back(x.i);
+            panels.push_back(x.k);
+        }
+    P->npanels = static_cast<int>(panels.size() / 3);
+    if (upload(&P->d_panels, panels) != cudaSuccess) return TQR_ERR_CUDA;
+    out = P;
+    return TQR_OK;
+}
+
+static int get_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    auto it = plans().find(key);
+    if (it != plans().end()) {
+        out = it->second;
+        return TQR_OK;
+    }
+    std::shared_ptr<Plan> P;
+    int rc = make_plan(key, P);
+    if (rc != TQR_OK) return rc;
+    plans()[key] = P;
+    out = P;
+    return TQR_OK;
+}
+
+static int get_apply_graph(Plan& P, int nstrips, bool trans, const DevGraph** out) {
+    std::lock_guard<std::mutex> lk(P.mu);
+    auto key = std::make_pair(nstrips, trans ? 1 : 0);
+    auto it = P.apply.find(key);
+    if (it == P.apply.end()) {
+        Graph g;
+        build_apply_graph(P.p, P.tt, nstrips, trans, g);
+        auto o = std::make_unique<DevGraphOwner>();
+        if (upload_graph(g, *o) != cudaSuccess) return TQR_ERR_CUDA;
+        it = P.apply.emplace(key, std::move(o)).first;
+    }
+    *out = &it->second->d;
+    return TQR_OK;
+}
+
+static double g_timeout_ms = 0.0;        // set by tqr_set_timeout_ms
+static int g_fault = 0;                  // set by tqr_inject_fault
+
+static uint64_t timeout_ns(double flops) {
+    if (g_timeout_ms > 0) return static_cast<uint64_t>(g_timeout_ms * 1e6);
+    if (const char* s = std::getenv("TQR_TIMEOUT_MS")) {
+        const double ms = std::atof(s);
+        if (ms > 0) return static_cast<uint64_t>(ms * 1e6);
+    }
+    // Longest legitimate wait is below the whole run; assume >= 50 GFLOP/s.
+    return static_cast<uint64_t>((10.0 + flops / 5e10) * 1e9);
+}
+
+static void free_state(ExecState& s) {
+    cudaFree(s.deps);
+    cudaFree(s.queue);
+    cudaFree(s.ctr);
+    s = ExecState();
+}
+
+static cudaError_t alloc_state(ExecState& s, int32_t cap, int32_t* status) {
+    free_state(s);
+    cudaError_t e;
+    const size_t n = std::max<int32_t>(1, cap);
+    if ((e = cudaMalloc(&s.deps, n * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.queue, n * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.ctr, 2 * sizeof(uint32_t))) != cudaSuccess) return e;
+    s.status = status;
+    s.capacity = cap;
+    return cudaSuccess;
+}
+
+}  // namespace tqr
+
+using namespace tqr;
+
+struct tqr_factors {
+    std::shared_ptr<Plan> plan;
+    double* A = nullptr;
+    cudaStream_t stream = nullptr;
+    double* tau_ge = nullptr;
+    double* tau_el = nullptr;
+    int32_t* status = nullptr;
+    ExecState fst, ast;
+    double* own_A = nullptr;     // device copies used by tqr_factor_host
+    double* own_B = nullptr;
+    size_t own_B_elems = 0;
+    ~tqr_factors() {
+        free_state(fst);
+        free_state(ast);
+        cudaFree(tau_ge);
+        cudaFree(tau_el);
+        cudaFree(status);
+        cudaFree(own_A);
+        cudaFree(own_B);
+    }
+};
+
+// A launch's graph, with the initially ready tasks dropped when a fault
+// injection is pending (the counters and edges are untouched).
+static DevGraph graph_for_launch(const DevGraph& g) {
+    DevGraph x = g;
+    if (g_fault == 1) {
+        x.nready = 0;
+        g_fault = 0;
+    }
+    return x;
+}
+
+static ExecParams base_params(const tqr_factors* f) {
+    const Plan& P = *f->plan;
+    ExecParams x{};
+    x.A = f->A;
+    x.lda = P.key.m;
+    x.m = P.key.m;
+    x.n = P.key.n;
+    x.nb = P.key.nb;
+    x.ib = P.key.ib;
+    x.p = P.p;
+    x.q = P.q;
+    x.tau_ge = f->tau_ge;
+    x.tau_el = f->tau_el;
+    x.trans = 1;
+    x.timeout_ns = timeout_ns(lapack_flops(P.key.m, P.key.n));
+    return x;
+}
+
+static int new_handle(const std::shared_ptr<Plan>& plan, tqr_factors** out) {
+    tqr_factors* f = new (std::nothrow) tqr_factors();
+    if (!f) return TQR_ERR_NOMEM;
+    f->plan = plan;
+    const size_t ntau = static_cast<size_t>(plan->p) * plan->q * plan->key.nb;
+    if (cudaMalloc(&f->tau_ge, ntau * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&f->tau_el, ntau * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&f->status, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(f->status, 0, sizeof(int32_t)) != cudaSuccess ||
+        alloc_state(f->fst, plan->dg.d.ntasks, f->status) != cudaSuccess) {
+        delete f;
+        return TQR_ERR_NOMEM;
+    }
+    *out = f;
+    return TQR_OK;
+}
+
+static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors** out) {
+    std::shared_ptr<Plan> plan;
+    int rc = get_plan(key, plan);
+    if (rc != TQR_OK) return rc;
+    tqr_factors* f = *out;
+    if (!f || f->plan != plan) {
+        rc = new_handle(plan, &f);
+        if (rc != TQR_OK) return rc;
+    }
+    f->A = A;
+    f->stream = static_cast<cudaStream_t>(stream);
+    ExecParams P = base_params(f);
+    cudaError_t e = launch_factor_exec(P, graph_for_launch(plan->dg.d), f->fst, plan->G, plan->smem, true,
+                                       f->stream);
+    *out = f;
+    return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+static int check_common(double* A, int64_t m, int64_t n, int nb, int ib) {
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (n < 1 || n > m) return -3;
+    if (nb < 4 || nb > 256 || nb % 4 != 0) return -4;
+    if (ib < 1 || ib > 64 || nb % ib != 0) return -5;
+    const int64_t p = (m + nb - 1) / nb, q = (n + nb - 1) / nb;
+    if (p > 65535 || q > 65535) return -2;
+    return TQR_OK;
+}
+
+extern "C" {
+
+int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, void* stream,
+               tqr_factors** out) {
+    try {
+        int rc = check_common(A, m, n, nb, ib);
+        if (rc != TQR_OK) return rc;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -6;
+        const int p = static_cast<int>((m + nb - 1) / nb);
+        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -7;
+        if (!out) return -9;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
+        PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
+                    tree == TQR_PLASMA ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
+        return run_factor(key, A, stream, out);
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_factor_list(double* A, int64_t m, int64_t n, int nb, int ib, const int32_t* list, int64_t count,
+                    int ts, void* stream, tqr_factors** out) {
+    try {
+        int rc = check_common(A, m, n, nb, ib);
+        if (rc != TQR_OK) return rc;
+        if (!list && count > 0) return -6;
+        if (count < 0) return -7;
+        if (ts != 0 && ts != 1) return -8;
+        if (!out) return -10;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
+        PlanKey key{m, n, nb, ib, -1, 0, ts, dev, {}};
+        key.list.resize(static_cast<size_t>(count));
+        for (int64_t t = 0; t < count; ++t) key.list[t] = {list[3 * t], list[3 * t + 1], list[3 * t + 2]};
+        const int p = static_cast<int>((m + nb - 1) / nb), q = static_cast<int>((n + nb - 1) / nb);
+        if (validate_elims(p, q, key.list.data(), count) != TQR_OK) return TQR_ERR_INVALID_LIST;
+        return run_factor(key, A, stream, out);
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+static int apply_common(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stream, bool trans) {
+    try {
+        if (!f || !f->plan) return -1;
+        if (!B) return -2;
+        const Plan& P = *f->plan;
+        if (ldb < P.key.m) return -3;
+        if (nrhs < 0) return -4;
+        if (nrhs == 0) return TQR_OK;
+        const int64_t ns = (nrhs + P.W - 1) / P.W;
+        if (ns * static_cast<int64_t>(P.npanels) > 0x7fffffff) return -4;
+        const DevGraph* g = nullptr;
+        int rc = get_apply_graph(*f->plan, static_cast<int>(ns), trans, &g);
+        if (rc != TQR_OK) return rc;
+        if (g->ntasks > f->ast.capacity) {
+            if (alloc_state(f->ast, g->ntasks, f->status) != cudaSuccess) return TQR_ERR_NOMEM;
+        }
+        f->stream = static_cast<cudaStream_t>(stream);
+        ExecParams x = base_params(f);
+        x.B = B;
+        x.ldb = ldb;
+        x.nrhs = nrhs;
+        x.trans = trans ? 1 : 0;
+        x.timeout_ns = timeout_ns(4.0 * static_cast<double>(P.key.m) * P.key.n * nrhs);
+        cudaError_t e = launch_factor_exec(x, graph_for_launch(*g), f->ast, P.G, P.smem, false, f->stream);
+        return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_apply_qt(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stream) {
+    return apply_common(f, B, ldb, nrhs, stream, true);
+}
+
+int tqr_apply_q(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stream) {
+    return apply_common(f, B, ldb, nrhs, stream, false);
+}
+
+int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream) {
+    try {
+        if (!f || !f->plan) return -1;
+        const Plan& P = *f->plan;
+        const size_t elems = static_cast<size_t>(P.p) * P.q * P.key.ib * P.key.nb;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (T_geqrt && cudaMemsetAsync(T_geqrt, 0, elems * sizeof(double), s) != cudaSuccess) return TQR_ERR_CUDA;
+        if (T_elim && cudaMemsetAsync(T_elim, 0, elems * sizeof(double), s) != cudaSuccess) return TQR_ERR_CUDA;
+        if (!T_geqrt && !T_elim) return TQR_OK;
+        ExecParams x = base_params(f);
+        f->stream = s;
+        return launch_form_t(x, P.d_panels, P.npanels, T_geqrt, T_elim, s) == cudaSuccess ? TQR_OK
+                                                                                           : TQR_ERR_CUDA;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_sync(tqr_factors* f) {
+    if (!f) return -1;
+    if (cudaStreamSynchronize(f->stream) != cudaSuccess) return TQR_ERR_CUDA;
+    int32_t st = 0;
+    if (cudaMemcpy(&st, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return TQR_ERR_CUDA;
+    return st;
+}
+
+int tqr_get_info(const tqr_factors* f, tqr_info* info) {
+    if (!f || !f->plan) return -1;
+    if (!info) return -2;
+    const Plan& P = *f->plan;
+    info->m = P.key.m;
+    info->n = P.key.n;
+    info->nb = P.key.nb;
+    info->ib = P.key.ib;
+    info->p = P.p;
+    info->q = P.q;
+    info->tree = P.key.tree;
+    info->BS = P.key.BS;
+    info->ts = P.ts ? 1 : 0;
+    info->strip = P.W;
+    info->n_elims = static_cast<int64_t>(P.elims.size());
+    info->n_tile_tasks = static_cast<int64_t>(P.tt.size());
+    info->n_device_tasks = P.dg.d.ntasks;
+    info->n_edges = P.dg.d.nedges;
+    info->critical_path = P.cp;
+    info->flops = lapack_flops(P.key.m, P.key.n);
+    return TQR_OK;
+}
+
+void tqr_free(tqr_factors* f) {
+    if (!f) return;
+    cudaStreamSynchronize(f->stream);
+    delete f;
+}
+
+int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS, double* B_host,
+                    int64_t nrhs, void* stream, tqr_factors** out) {
+    try {
+        if (!A_host) return -1;
+        if (!out) return -11;
+        if (B_host && nrhs < 0) return -9;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        tqr_factors* prev = *out;
+        double* dA = prev ? prev->own_A : nullptr;
+        const bool same = prev && prev->plan && prev->plan->key.m == m && prev->plan->key.n == n && dA;
+        if (!same) {
+            if (cudaMalloc(&dA, static_cast<size_t>(m) * n * sizeof(double)) != cudaSuccess) return TQR_ERR_NOMEM;
+        }
+        if (cudaMemcpyAsync(dA, A_host, static_cast<size_t>(m) * n * sizeof(double), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return TQR_ERR_CUDA;
+        tqr_factors* f = same ? prev : nullptr;
+        int rc = tqr_factor(dA, m, n, nb, ib, tree, BS, stream, &f);
+        if (rc != TQR_OK) {
+            if (!same) cudaFree(dA);
+            return rc;
+        }
+        if (f != prev) {
+            f->own_A = dA;            // new handle adopts the buffer
+        }
+        if (B_host && nrhs > 0) {
+            const size_t be = static_cast<size_t>(m) * nrhs;
+            if (f->own_B_elems < be) {
+                cudaFree(f->own_B);
+                f->own_B = nullptr;
+                f->own_B_elems = 0;
+                if (cudaMalloc(&f->own_B, be * sizeof(double)) != cudaSuccess) return TQR_ERR_NOMEM;
+                f->own_B_elems = be;
+            }
+            if (cudaMemcpyAsync(f->own_B, B_host, be * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return TQR_ERR_CUDA;
+            rc = tqr_apply_qt(f, f->own_B, m, nrhs, stream);
+            if (rc != TQR_OK) return rc;
+            if (cudaMemcpyAsync(B_host, f->own_B, be * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return TQR_ERR_CUDA;
+        }
+        if (cudaMemcpyAsync(A_host, dA, static_cast<size_t>(m) * n * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+            return TQR_ERR_CUDA;
+        *out = f;
+        return tqr_sync(f);
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+// ------------------------------------------------------------- host only
+int tqr_elimination_list(int p, int q, int tree, int BS, int32_t* out, int64_t cap, int64_t* count) {
+    try {
+        if (p < 1 || p > 65535) return -1;
+        if (q < 1 || q > p) return -2;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (!count) return -7;
+        std::vector<Elim> el;
+        int rc = make_elims(p, q, tree, BS, el);
+        if (rc != TQR_OK) return rc;
+        *count = static_cast<int64_t>(el.size());
+        if (static_cast<int64_t>(el.size()) > cap) return TQR_ERR_CAPACITY;
+        if (!out && !el.empty()) return -5;
+        for (size_t t = 0; t < el.size(); ++t) {
+            out[3 * t] = el[t].i;
+            out[3 * t + 1] = el[t].piv;
+            out[3 * t + 2] = el[t].k;
+        }
+        return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_validate_list(int p, int q, const int32_t* list, int64_t count) {
+    try {
+        if (p < 1) return -1;
+        if (q < 1 || q > p) return -2;
+        if (!list && count > 0) return -3;
+        if (count < 0) return -4;
+        std::vector<Elim> el(static_cast<size_t>(count));
+        for (int64_t t = 0; t < count; ++t) el[t] = {list[3 * t], list[3 * t + 1], list[3 * t + 2]};
+        return validate_elims(p, q, el.data(), count);
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero_time) {
+    try {
+        if (p < 1 || p > 65535) return -1;
+        if (q < 1 || q > p) return -2;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (!cp) return -5;
+        std::vector<Elim> el;
+        int rc = make_elims(p, q, tree, BS, el);
+        if (rc != TQR_OK) return rc;
+        std::vector<TileTask> tt;
+        expand_tasks(p, q, el, tree == TQR_FLAT_TS, tt);
+        std::vector<int64_t> fin;
+        *cp = simulate(p, q, tt, &fin);
+        if (zero_time) {
+            for (int64_t t = 0; t < static_cast<int64_t>(p) * q; ++t) zero_time[t] = -1;
+            for (size_t t = 0; t < tt.size(); ++t)
+                if (tt[t].kind == TTQRT || tt[t].kind == TSQRT)
+                    zero_time[static_cast<int64_t>(tt[t].i) * q + tt[t].k] = static_cast<int32_t>(fin[t]);
+        }
+        return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int64_t cap, int64_t* count) {
+    try {
+        if (p < 1 || p > 65535) return -1;
+        if (q < 1 || q > p) return -2;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (!count) return -8;
+        std::vector<Elim> el;
+        int rc = make_elims(p, q, tree, BS, el);
+        if (rc != TQR_OK) return rc;
+        std::vector<TileTask> tt;
+        expand_tasks(p, q, el, tree == TQR_FLAT_TS, tt);
+        *count = static_cast<int64_t>(tt.size());
+        if (static_cast<int64_t>(tt.size()) > cap) return TQR_ERR_CAPACITY;
+        if (!out && !tt.empty()) return -5;
+        std::vector<int64_t> fin;
+        simulate(p, q, tt, &fin);
+        for (size_t t = 0; t < tt.size(); ++t) {
+            out[5 * t] = tt[t].kind;
+            out[5 * t + 1] = tt[t].i;
+            out[5 * t + 2] = tt[t].piv;
+            out[5 * t + 3] = tt[t].k;
+            out[5 * t + 4] = tt[t].j;
+            if (finish) finish[t] = fin[t];
+        }
+        return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_set_timeout_ms(double ms) {
+    g_timeout_ms = ms > 0 ? ms : 0.0;
+    return TQR_OK;
+}
+
+int tqr_inject_fault(int kind) {
+    if (kind != 0 && kind != 1) return -1;
+    g_fault = kind;
+    return TQR_OK;
+}
+
+const char* tqr_strerror(int status) {
+    switch (status) {
+        case TQR_OK: return "success";
+        case TQR_ERR_INVALID_LIST: return "invalid elimination list";
+        case TQR_ERR_TIMEOUT: return "device wait timed out";
+        case TQR_ERR_NONFINITE: return "non-finite value in a Householder norm";
+        case TQR_ERR_CUDA: return "CUDA runtime error";
+        case TQR_ERR_NOMEM: return "out of memory";
+        case TQR_ERR_CAPACITY: return "output array too small";
+        case TQR_ERR_INTERNAL: return "internal error";
+        case TQR_ERR_UNSUPPORTED: return "unsupported parameters";
+        default:
+            if (status < 0 && status > -100) return "invalid argument";
+            return "unknown status";
+    }
+}
+
+}  // extern "C"

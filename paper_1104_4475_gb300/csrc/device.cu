@@ -1,0 +1,611 @@
+// Device side of libtqr: the persistent DAG executor and the six FP64 tile
+// kernels of tiled Householder QR ("Tiled QR factorization algorithms",
+// Bouwmeester, Jacquelin, Langou, Robert, 2011; kernels of Section 2.1,
+// execution scheme of Section 2.3).
+//
+// Design (sm_103a, FP64):
+//  * One persistent launch runs a whole task graph.  Each CTA pops a task id
+//    from a global ready queue, runs the task with all 256 threads, then
+//    decrements its successors' dependency counters and pushes the ones that
+//    reach zero.  Every wait is bounded by a %globaltimer limit; on expiry the
+//    CTA records TQR_ERR_TIMEOUT in the status word and returns.
+//  * FP64 arithmetic runs on the DFMA pipe (sm_103 has no FP64 tensor path
+//    faster than DFMA), so the kernels apply Householder reflectors one at a
+//    time: no T-factor products are spent on the critical path, and every
+//    flop is one the LAPACK count includes.  ib only sets how many reflectors
+//    are staged in shared memory at once (and the block size of T).
+//  * An update kernel works on a strip of W = 256/G columns held in shared
+//    memory.  Thread (c, g) owns column c and the rows r = g (mod G) of the
+//    strip, so a reflector's dot product is a G-lane shuffle reduction and no
+//    thread ever reads a row another thread writes.
+#include "tqr_internal.h"
+#include "../../include/tqr.h"
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tqr {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Mode { GE = 0, TT = 1, TS = 2 };
+
+// ------------------------------------------------------------ memory order
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int atom_add_acq_rel(int32_t* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------ smem layout
+struct Smem {
+    double* Cs;    // strip: nb x W, leading dimension ldc
+    double* Vs;    // reflector block: nb x ib, leading dimension nb
+    double* Ct;    // top rows: ib x max(W, ib), leading dimension ldt
+    double* taus;  // ib
+    int ldc, ldt;
+};
+
+__host__ __device__ inline int round16(int x) { return (x + 15) / 16 * 16; }
+__host__ __device__ inline int ldc_of(int nb, int G) { return round16(nb) + (G % 16); }
+
+__host__ __device__ inline int smem_doubles(int nb, int ib, int G) {
+    const int W = kThreads / G;
+    const int wt = W > ib ? W : ib;
+    return ldc_of(nb, G) * W + nb * ib + (ib + 1) * wt + ib;
+}
+
+template <int G>
+__device__ __forceinline__ Smem layout(const ExecParams& P, double* base) {
+    constexpr int W = kThreads / G;
+    Smem s;
+    s.ldc = ldc_of(P.nb, G);
+    s.ldt = P.ib + 1;
+    s.Cs = base;
+    s.Vs = s.Cs + s.ldc * W;
+    s.Ct = s.Vs + P.nb * P.ib;
+    const int wt = W > P.ib ? W : P.ib;
+    s.taus = s.Ct + s.ldt * wt;
+    return s;
+}
+
+// A view of (a window of) a column-major matrix with validity bounds: rows
+// >= rv and columns >= cv do not exist (they read as zero, never written).
+struct View {
+    double* p;
+    int64_t ld;
+    int rv, cv;
+};
+
+__device__ __forceinline__ View tile_view(const ExecParams& P, int i, int k) {
+    View v;
+    v.p = P.A + static_cast<int64_t>(k) * P.nb * P.lda + static_cast<int64_t>(i) * P.nb;
+    v.ld = P.lda;
+    const int64_t rr = P.m - static_cast<int64_t>(i) * P.nb;
+    const int64_t cc = P.n - static_cast<int64_t>(k) * P.nb;
+    v.rv = static_cast<int>(rr < P.nb ? rr : P.nb);
+    v.cv = static_cast<int>(cc < P.nb ? cc : P.nb);
+    return v;
+}
+
+// Row block i of the right-hand side B, columns from c0.
+__device__ __forceinline__ View rhs_view(const ExecParams& P, int i, int c0) {
+    View v;
+    v.p = P.B + static_cast<int64_t>(c0) * P.ldb + static_cast<int64_t>(i) * P.nb;
+    v.ld = P.ldb;
+    const int64_t rr = P.m - static_cast<int64_t>(i) * P.nb;
+    const int64_t cc = P.nrhs - c0;
+    v.rv = static_cast<int>(rr < P.nb ? rr : P.nb);
+    v.cv = static_cast<int>(cc < 0x40000000 ? cc : 0x40000000);
+    return v;
+}
+
+// dst[(r - rbase) + c*ldd] = src(r, c0 + c) for r in [r0, r1), c in [0, nc).
+__device__ __forceinline__ void load_rect(double* dst, int ldd, int rbase, const View& v, int r0,
+                                          int r1, int c0, int nc) {
+    const int nr = r1 - r0;
+    if (nr <= 0) return;
+    for (int idx = threadIdx.x; idx < nr * nc; idx += kThreads) {
+        const int r = r0 + idx % nr;
+        const int c = idx / nr;
+        double x = 0.0;
+        if (r < v.rv && c0 + c < v.cv) x = __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld);
+        dst[(r - rbase) + c * ldd] = x;
+    }
+}
+
+// src(r, c0 + c) = dst[...] for the same rectangle; upper = only r <= c0 + c.
+__device__ __forceinline__ void store_rect(const double* src, int lds, int rbase, const View& v,
+                                           int r0, int r1, int c0, int nc, bool upper) {
+    const int nr = r1 - r0;
+    if (nr <= 0) return;
+    for (int idx = threadIdx.x; idx < nr * nc; idx += kThreads) {
+        const int r = r0 + idx % nr;
+        const int c = idx / nr;
+        if (r < v.rv && c0 + c < v.cv && (!upper || r <= c0 + c))
+            v.p[r + static_cast<int64_t>(c0 + c) * v.ld] = src[(r - rbase) + c * lds];
+    }
+}
+
+template <int G>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// ----------------------------------------------------------------------------
+// Apply reflectors j0..j0+ib-1 (staged in Vs/taus) to the strip in Cs (and
+// the top rows in Ct for TT/TS), forward (Q^T) or backward (Q).
+//   GE: reflector j is (1 at row j, Vs[r>j]) on the strip's own rows;
+//   TT: (1 at top row j, Vs[0..j] on the bottom rows);
+//   TS: (1 at top row j, Vs[0..nb-1] on the bottom rows).
+// Thread (c, g) owns column c and rows r = g (mod G): no shared-memory
+// hazards between threads, only the G-lane reductions.
+// ----------------------------------------------------------------------------
+template <int G, int MODE>
+__device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int ib, int trans) {
+    const int c = threadIdx.x / G;
+    const int g = threadIdx.x % G;
+    double* Cc = S.Cs + c * S.ldc;
+    for (int s = 0; s < ib; ++s) {
+        const int jj = trans ? s : ib - 1 - s;
+        const int j = j0 + jj;
+        const double tau = S.taus[jj];
+        const double* v = S.Vs + jj * nb;
+        int rlo, rhi;   // own rows r in [rlo, rhi), r = g (mod G)
+        double acc;
+        if (MODE == GE) {
+            rlo = j + 1 + ((g - j - 1) & (G - 1));
+            rhi = nb;
+            acc = (g == (j & (G - 1))) ? Cc[j] : 0.0;
+        } else {
+            rlo = g;
+            rhi = (MODE == TT) ? j + 1 : nb;
+            acc = (g == 0) ? S.Ct[jj + c * S.ldt] : 0.0;
+        }
+        double acc2 = 0.0;
+        int r = rlo;
+        for (; r + G < rhi; r += 2 * G) {
+            acc = fma(v[r], Cc[r], acc);
+            acc2 = fma(v[r + G], Cc[r + G], acc2);
+        }
+        if (r < rhi) acc = fma(v[r], Cc[r], acc);
+        acc = group_sum<G>(acc + acc2);
+        const double w = tau * acc;
+        if (MODE == GE) {
+            if (g == (j & (G - 1))) Cc[j] -= w;
+        } else {
+            if (g == 0) S.Ct[jj + c * S.ldt] -= w;
+        }
+        for (r = rlo; r < rhi; r += G) Cc[r] = fma(-v[r], w, Cc[r]);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Householder panel factorization of the ib columns staged in Vs (and Ct for
+// TT/TS).  Reflector j maps (alpha, x) to (beta, 0), LAPACK convention:
+// beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha)/beta,
+// v = x / (alpha - beta); x = 0 gives tau = 0.
+//   GE: alpha = Vs[j, jj], x = Vs[j+1.., jj]   (GEQRT)
+//   TT: alpha = Ct[jj, jj], x = Vs[0..j, jj]   (TTQRT)
+//   TS: alpha = Ct[jj, jj], x = Vs[0..nb-1, jj] (TSQRT)
+// Warp 0 forms each reflector; the 8 warps then update the remaining panel
+// columns, one column per warp at a time.
+// ----------------------------------------------------------------------------
+template <int MODE>
+__device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* status) {
+    __shared__ double s_scale;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    for (int jj = 0; jj < ib; ++jj) {
+        const int j = j0 + jj;
+        double* v = S.Vs + jj * nb;
+        const int rlo = (MODE == GE) ? j + 1 : 0;
+        const int rhi = (MODE == TT) ? j + 1 : nb;
+        if (warp == 0) {
+            double sig = 0.0;
+            for (int r = rlo + lane; r < rhi; r += 32) sig = fma(v[r], v[r], sig);
+            sig = warp_sum(sig);
+            if (lane == 0) {
+                double* ap = (MODE == GE) ? &v[j] : &S.Ct[jj + jj * S.ldt];
+                const double alpha = *ap;
+                double tau = 0.0, scale = 0.0;
+                if (sig != 0.0 || !isfinite(sig)) {
+                    const double nrm = sqrt(fma(alpha, alpha, sig));
+                    if (!isfinite(nrm)) set_status(status, TQR_ERR_NONFINITE);
+                    const double beta = alpha >= 0.0 ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                    *ap = beta;
+                } else {
+                    scale = 0.0;   // x is zero: identity reflector, zero tail
+                }
+                S.taus[jj] = tau;
+                s_scale = scale;
+            }
+            __syncwarp();
+            const double sc = s_scale;
+            for (int r = rlo + lane; r < rhi; r += 32) v[r] *= sc;
+        }
+        __syncthreads();
+        const double tau = S.taus[jj];
+        for (int cc = jj + 1 + warp; cc < ib; cc += kThreads / 32) {
+            double* u = S.Vs + cc * nb;
+            double acc = 0.0;
+            for (int r = rlo + lane; r < rhi; r += 32) acc = fma(v[r], u[r], acc);
+            if (lane == 0) acc += (MODE == GE) ? u[j] : S.Ct[jj + cc * S.ldt];
+            acc = warp_sum(acc);
+            const double w = tau * acc;
+            if (lane == 0) {
+                if (MODE == GE) u[j] -= w;
+                else S.Ct[jj + cc * S.ldt] -= w;
+            }
+            for (int r = rlo + lane; r < rhi; r += 32) u[r] = fma(-v[r], w, u[r]);
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Panel kernels: GEQRT(i,k) (MODE GE), TTQRT(i,piv,k) (TT), TSQRT(i,piv,k)
+// (TS).  Blocks of ib columns are factored in turn; after each block its
+// reflectors are applied to the rest of the tile (pair), W columns at a time.
+// ----------------------------------------------------------------------------
+template <int G, int MODE>
+__device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* smem) {
+    constexpr int W = kThreads / G;
+    const Smem S = layout<G>(P, smem);
+    const int nb = P.nb, ib = P.ib;
+    const View bot = tile_view(P, i, k);                    // GE: the tile itself
+    const View top = (MODE == GE) ? bot : tile_view(P, piv, k);
+    double* tau_out = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
+    const int ncol = bot.cv;                                // valid columns of the tile pair
+    for (int j0 = 0; j0 < nb; j0 += ib) {
+        // Stage the panel block.
+        __syncthreads();
+        if (MODE == GE) {
+            load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
+        } else {
+            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib);
+            load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
+        }
+        __syncthreads();
+        factor_block<MODE>(S, nb, j0, ib, P.status);
+        // Write the block back: R (and V) in place, tau to the handle.
+        if (MODE == GE) {
+            store_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib, false);
+        } else {
+            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib, true);
+            store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
+        }
+        for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
+        // Trailing update of the columns right of the block.
+        for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
+            __syncthreads();
+            if (MODE == GE) {
+                load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
+            } else {
+                load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
+                load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
+            }
+            __syncthreads();
+            apply_block<G, MODE>(S, nb, j0, ib, 1);
+            __syncthreads();
+            if (MODE == GE) {
+                store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
+            } else {
+                store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+                store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Update kernels on one strip: UNMQR (GE), TTMQR (TT), TSMQR (TS).  The
+// reflectors come from tile (i,k); the strip is columns [strip*W, +W) of
+// tile column j (rows i and piv), or of the right-hand side B.
+// ----------------------------------------------------------------------------
+template <int G, int MODE>
+__device__ void update_task(const ExecParams& P, const DevTask& T, double* smem) {
+    constexpr int W = kThreads / G;
+    const Smem S = layout<G>(P, smem);
+    const int nb = P.nb, ib = P.ib;
+    const View vt = tile_view(P, T.i, T.k);
+    const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(T.k) * P.p + T.i) * nb;
+    const int c0 = T.strip * W;
+    View bot, top;
+    if (P.B) {
+        bot = rhs_view(P, T.i, 0);
+        top = (MODE == GE) ? bot : rhs_view(P, T.piv, 0);
+    } else {
+        bot = tile_view(P, T.i, T.j);
+        top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
+    }
+    const int vrows_hi = nb;
+    load_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W);
+    const int nblk = nb / ib;
+    for (int bb = 0; bb < nblk; ++bb) {
+        const int b = P.trans ? bb : nblk - 1 - bb;
+        const int j0 = b * ib;
+        __syncthreads();
+        if (MODE == GE) load_rect(S.Vs, nb, 0, vt, j0, vrows_hi, j0, ib);
+        else load_rect(S.Vs, nb, 0, vt, 0, (MODE == TT) ? j0 + ib : vrows_hi, j0, ib);
+        for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
+        if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
+        __syncthreads();
+        apply_block<G, MODE>(S, nb, j0, ib, P.trans);
+        if (MODE != GE) {
+            __syncthreads();
+            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+        }
+    }
+    __syncthreads();
+    store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
+}
+
+template <int G>
+__device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
+    switch (T.kind) {
+        case GEQRT: panel_task<G, GE>(P, T.i, -1, T.k, smem); break;
+        case TTQRT: panel_task<G, TT>(P, T.i, T.piv, T.k, smem); break;
+        case TSQRT: panel_task<G, TS>(P, T.i, T.piv, T.k, smem); break;
+        case UNMQR: update_task<G, GE>(P, T, smem); break;
+        case TTMQR: update_task<G, TT>(P, T, smem); break;
+        case TSMQR: update_task<G, TS>(P, T, smem); break;
+        default: set_status(P.status, TQR_ERR_INTERNAL); break;
+    }
+}
+
+// Warp 0: decrement the successors of task t; push those that become ready.
+__device__ void release_successors(const ExecParams& P, int t) {
+    const int lane = threadIdx.x & 31;
+    __threadfence();                      // the CTA's writes before the counters
+    const int b = P.succ_ptr[t], e = P.succ_ptr[t + 1];
+    for (int base = b; base < e; base += 32) {
+        const int idx = base + lane;
+        int s = -1;
+        bool ready = false;
+        if (idx < e) {
+            s = P.succ[idx];
+            ready = atom_add_acq_rel(&P.deps[s], -1) == 1;
+        }
+        const unsigned mask = __ballot_sync(kFull, ready);
+        if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned pos = 0;
+            if (lane == leader) pos = atomicAdd(&P.ctr[1], static_cast<unsigned>(__popc(mask)));
+            pos = __shfl_sync(kFull, pos, leader);
+            if (ready) {
+                const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+                if (pos + rank < static_cast<unsigned>(P.ntasks)) st_release(&P.queue[pos + rank], s);
+                else set_status(P.status, TQR_ERR_INTERNAL);
+            }
+        }
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int s_task;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = -1;
+            const unsigned slot = atomicAdd(&P.ctr[0], 1u);
+            if (slot < static_cast<unsigned>(P.ntasks)) {
+                const uint64_t t0 = globaltimer();
+                unsigned it = 0;
+                for (;;) {
+                    t = ld_acquire(&P.queue[slot]);
+                    if (t >= 0) break;
+                    if (ld_relaxed(P.status) != 0) break;
+                    if ((++it & 31u) == 0 && globaltimer() - t0 > P.timeout_ns) {
+                        set_status(P.status, TQR_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                if (t >= P.ntasks) {
+                    set_status(P.status, TQR_ERR_INTERNAL);
+                    t = -1;
+                }
+                if (t >= 0) __threadfence();
+            }
+            s_task = t;
+        }
+        __syncthreads();
+        const int t = s_task;
+        if (t < 0) return;
+        const DevTask T = P.tasks[t];
+        run_task<G>(P, T, smem);
+        __syncthreads();
+        if (threadIdx.x < 32) release_successors(P, t);
+    }
+}
+
+__global__ void init_kernel(int32_t* deps, const int32_t* indeg, int32_t* queue, const int32_t* ready,
+                            int nready, int ntasks, uint32_t* ctr, int32_t* status, int reset) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += stride) {
+        deps[t] = indeg[t];
+        queue[t] = (t < nready) ? ready[t] : -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr[0] = 0;
+        ctr[1] = static_cast<uint32_t>(nready);
+        if (reset) *status = 0;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// T factors from stored reflectors (Schreiber-Van Loan forward accumulation):
+// for each block of ib reflectors, T[:c, c] = -tau_c T[:c, :c] (V^T v_c),
+// T[c, c] = tau_c, with v the full reflector vectors of the kernel.
+// One CTA per panel task; panels[3*t] = kind, [3*t+1] = i, [3*t+2] = k.
+// ----------------------------------------------------------------------------
+__global__ void form_t_kernel(ExecParams P, const int32_t* panels, double* T_ge, double* T_el) {
+    extern __shared__ __align__(16) double sm[];
+    const int kind = panels[3 * blockIdx.x];
+    const int i = panels[3 * blockIdx.x + 1];
+    const int k = panels[3 * blockIdx.x + 2];
+    const int nb = P.nb, ib = P.ib;
+    double* Tout = (kind == GEQRT) ? T_ge : T_el;
+    if (!Tout) return;
+    Tout += (static_cast<int64_t>(k) * P.p + i) * ib * nb;
+    const double* tau = ((kind == GEQRT) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
+    const View v = tile_view(P, i, k);
+    double* Vb = sm;                 // nb x ib
+    double* Tb = sm + nb * ib;       // ib x ib
+    double* gv = Tb + ib * ib;       // ib
+    for (int j0 = 0; j0 < nb; j0 += ib) {
+        __syncthreads();
+        load_rect(Vb, nb, 0, v, 0, nb, j0, ib);
+        for (int t = threadIdx.x; t < ib * ib; t += blockDim.x) Tb[t] = 0.0;
+        __syncthreads();
+        for (int c = 0; c < ib; ++c) {
+            const int jc = j0 + c;
+            // g[r] = v_r^T v_c for r < c (full vectors: unit entry + tail).
+            for (int r = threadIdx.x; r < c; r += blockDim.x) {
+                const int jr = j0 + r;
+                double s = 0.0;
+                if (kind == GEQRT) {
+                    s = Vb[jc + r * nb];                            // tail_r . e_c
+                    for (int x = jc + 1; x < nb; ++x) s = fma(Vb[x + r * nb], Vb[x + c * nb], s);
+                } else {
+                    const int hi = (kind == TTQRT) ? jr + 1 : nb;   // tail_r support
+                    for (int x = 0; x < hi; ++x) s = fma(Vb[x + r * nb], Vb[x + c * nb], s);
+                }
+                gv[r] = s;
+            }
+            __syncthreads();
+            const double tc = tau[jc];
+            for (int r = threadIdx.x; r < c; r += blockDim.x) {
+                double s = 0.0;
+                for (int x = r; x < c; ++x) s = fma(Tb[r + x * ib], gv[x], s);
+                Tb[r + c * ib] = -tc * s;
+            }
+            if (threadIdx.x == 0) Tb[c + c * ib] = tc;
+            __syncthreads();
+        }
+        for (int t = threadIdx.x; t < ib * ib; t += blockDim.x) {
+            const int r = t % ib, c = t / ib;
+            Tout[r + static_cast<int64_t>(j0 + c) * ib] = Tb[t];
+        }
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Host-side launch helpers.
+// ----------------------------------------------------------------------------
+int strip_width(int G) { return kThreads / G; }
+
+bool choose_layout(int nb, int ib, int* G, int* smem_bytes) {
+    int dev = 0, maxsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        maxsm = 232448;
+    const int budget = maxsm - 1024;   // static shared memory of the kernel
+    const int cands[3] = {4, 8, 16};
+    for (int g : cands) {
+        const int W = kThreads / g;
+        if (W > nb && g != 16) continue;
+        const int bytes = smem_doubles(nb, ib, g) * static_cast<int>(sizeof(double));
+        if (bytes <= budget) {
+            *G = g;
+            *smem_bytes = bytes;
+            return true;
+        }
+    }
+    return false;
+}
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int G>
+static cudaError_t launch_g(const ExecParams& P, int smem, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(exec_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    exec_kernel<G><<<grid, kThreads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G, int smem,
+                               bool reset_status, cudaStream_t s) {
+    if (g.ntasks > st.capacity) return cudaErrorInvalidValue;
+    P.tasks = g.tasks;
+    P.succ_ptr = g.succ_ptr;
+    P.succ = g.succ;
+    P.deps = st.deps;
+    P.queue = st.queue;
+    P.ctr = st.ctr;
+    P.status = st.status;
+    P.ntasks = g.ntasks;
+    const int nsm = device_sm_count();
+    int ib = (g.ntasks + 255) / 256;
+    if (ib > 4 * nsm) ib = 4 * nsm;
+    if (ib < 1) ib = 1;
+    init_kernel<<<ib, 256, 0, s>>>(st.deps, g.indeg, st.queue, g.ready, g.nready, g.ntasks, st.ctr, st.status,
+                                  reset_status ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (g.ntasks == 0) return cudaSuccess;
+    int grid = nsm > 0 ? nsm : 1;                 // one 256-thread CTA per SM
+    if (grid > g.ntasks) grid = g.ntasks;
+    switch (G) {
+        case 4: return launch_g<4>(P, smem, grid, s);
+        case 8: return launch_g<8>(P, smem, grid, s);
+        case 16: return launch_g<16>(P, smem, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_form_t(const ExecParams& P, const int32_t* panels, int npanels, double* T_ge,
+                          double* T_el, cudaStream_t s) {
+    if (npanels == 0) return cudaSuccess;
+    const int smem = (P.nb * P.ib + P.ib * P.ib + P.ib) * static_cast<int>(sizeof(double));
+    cudaError_t e = cudaFuncSetAttribute(form_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    form_t_kernel<<<npanels, kThreads, smem, s>>>(P, panels, T_ge, T_el);
+    return cudaGetLastError();
+}
+
+}  // namespace tqr

@@ -1,0 +1,326 @@
+// Host planner of libtqr: elimination lists of the seven trees, the validity
+// rules of an elimination list, the TS/TT expansion into kernel tasks, the
+// unit-weight critical-path simulator, and the device task graphs.
+//
+// Paper: "Tiled QR factorization algorithms" (Bouwmeester, Jacquelin, Langou,
+// Robert, 2011).  All indices here are 0-based.
+#include "tqr_internal.h"
+#include "../../include/tqr.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace tqr {
+
+// ---------------------------------------------------------------------------
+// Elimination lists (Section 3).
+// ---------------------------------------------------------------------------
+
+// Sameh-Kuck / FlatTree: column k zeroes rows k+1..p-1 with the panel row k.
+static void flat_list(int p, int q, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    for (int k = 0; k < qq; ++k)
+        for (int i = k + 1; i < p; ++i) out.push_back({i, k, k});
+}
+
+// BinaryTree (Proposition 1): level s = 1,2,4,... zeroes the rows whose
+// offset d from the panel row is an odd multiple of s, with the row s above.
+static void binary_list(int p, int q, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    for (int k = 0; k < qq; ++k) {
+        const int rows = p - k;
+        for (int s = 1; s < rows; s *= 2)
+            for (int d = s; d < rows; d += 2 * s) out.push_back({k + d, k + d - s, k});
+    }
+}
+
+// Fibonacci scheme of order 1 (Section 3.1).  In column 1 the rows at offset
+// r = i - k + 1 (1-based) from the panel row fall into groups y = 1, 2, ...
+// holding the offsets y(y-1)/2+2 .. y(y+1)/2+1; group y is zeroed at coarse
+// step x - y + 1, larger groups first.  Column k repeats the pattern shifted
+// down by k-1 rows, the bottom group being cut at row p.  Each row of a
+// group of z rows is paired with the row z above it.
+static void fibonacci_list(int p, int q, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    for (int k = 0; k < qq; ++k) {
+        const int rmax = p - k;                    // largest offset r in this column
+        if (rmax < 2) continue;
+        int ymax = 1;
+        while (ymax * (ymax + 1) / 2 + 1 < rmax) ++ymax;
+        for (int y = ymax; y >= 1; --y) {
+            const int lo = y * (y - 1) / 2 + 2;
+            const int hi = std::min(y * (y + 1) / 2 + 1, rmax);
+            const int z = hi - lo + 1;
+            for (int r = lo; r <= hi; ++r) {
+                const int i = k + r - 1;           // 0-based row of offset r
+                out.push_back({i, i - z, k});
+            }
+        }
+    }
+}
+
+// Greedy for tiles (Algorithm 4).  nT[j] / nZ[j] count the tiles of column j
+// that are triangularized / zeroed, from the bottom row upwards.  Each outer
+// step sweeps j from right to left, so column j reads nZ[j-1] as it stood at
+// the end of the previous step.  The loop ends when every column
+// j < min(p,q) holds p-1-j zeros.
+static void greedy_list(int p, int q, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    std::vector<int> nZ(q, 0), nT(q, 0);
+    auto finished = [&]() {
+        for (int j = 0; j < qq; ++j)
+            if (nZ[j] != p - 1 - j) return false;
+        return true;
+    };
+    while (!finished()) {
+        for (int j = q - 1; j >= 0; --j) {
+            const int tri = (j == 0) ? p : nZ[j - 1];
+            const int zn = nZ[j] + (nT[j] - nZ[j]) / 2;
+            const int shift = zn - nZ[j];
+            for (int kk = nZ[j]; kk < zn; ++kk) {
+                const int row = p - 1 - kk;
+                out.push_back({row, row - shift, j});
+            }
+            nT[j] = tri;
+            nZ[j] = zn;
+        }
+    }
+}
+
+// PlasmaTree(BS) (Section 3.2): flat trees inside domains of BS rows that
+// start at the panel row (the bottom domain shrinks as k grows), then a binary
+// merge of the domain heads.
+static void plasma_list(int p, int q, int BS, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    std::vector<int> heads;
+    for (int k = 0; k < qq; ++k) {
+        heads.clear();
+        for (int h = k; h < p; h += BS) heads.push_back(h);
+        for (int h : heads)
+            for (int i = h + 1; i < std::min(h + BS, p); ++i) out.push_back({i, h, k});
+        const int nh = static_cast<int>(heads.size());
+        for (int s = 1; s < nh; s *= 2)
+            for (int d = s; d < nh; d += 2 * s) out.push_back({heads[d], heads[d - s], k});
+    }
+}
+
+int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out) {
+    out.clear();
+    switch (tree) {
+        case TQR_FLAT_TS:
+        case TQR_FLAT_TT:
+        case TQR_SAMEH_KUCK: flat_list(p, q, out); return TQR_OK;
+        case TQR_BINARY: binary_list(p, q, out); return TQR_OK;
+        case TQR_FIBONACCI: fibonacci_list(p, q, out); return TQR_OK;
+        case TQR_GREEDY: greedy_list(p, q, out); return TQR_OK;
+        case TQR_PLASMA:
+            if (BS < 1 || BS > p) return -4;
+            plasma_list(p, q, BS, out);
+            return TQR_OK;
+        default: return -3;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Validity rules (Section 2.2).
+// ---------------------------------------------------------------------------
+int validate_elims(int p, int q, const Elim* e, int64_t count) {
+    const int qq = std::min(p, q);
+    if (p < 1 || q < 1 || p < q) return TQR_ERR_INVALID_LIST;
+    std::vector<int64_t> pos(static_cast<size_t>(p) * qq, -1);
+    auto at = [&](int i, int k) -> int64_t& { return pos[static_cast<size_t>(k) * p + i]; };
+    for (int64_t t = 0; t < count; ++t) {
+        const Elim& x = e[t];
+        if (x.k < 0 || x.k >= qq) return TQR_ERR_INVALID_LIST;
+        if (x.i <= x.k || x.i >= p) return TQR_ERR_INVALID_LIST;
+        if (x.piv < x.k || x.piv >= p || x.piv == x.i) return TQR_ERR_INVALID_LIST;
+        if (at(x.i, x.k) >= 0) return TQR_ERR_INVALID_LIST;   // zeroed twice
+        at(x.i, x.k) = t;
+    }
+    for (int k = 0; k < qq; ++k)
+        for (int i = k + 1; i < p; ++i)
+            if (at(i, k) < 0) return TQR_ERR_INVALID_LIST;    // never zeroed
+    for (int64_t t = 0; t < count; ++t) {
+        const Elim& x = e[t];
+        for (int kp = 0; kp < x.k; ++kp)                         // both rows ready
+            if (at(x.i, kp) > t || at(x.piv, kp) > t) return TQR_ERR_INVALID_LIST;
+        if (x.piv > x.k && at(x.piv, x.k) < t) return TQR_ERR_INVALID_LIST;  // annihilator
+    }
+    return TQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TS / TT expansion (Algorithms 2 and 3).  A tile already in triangle form
+// is not factored again.  In TT every tile (x,k), x >= k, is factored once,
+// at the first elimination of column k that involves row x; the diagonal
+// tile of the last column of a square matrix, which takes part in no
+// elimination, is factored at the end.
+// ---------------------------------------------------------------------------
+void expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out) {
+    out.clear();
+    std::vector<char> tri(static_cast<size_t>(p) * q, 0);
+    auto factor = [&](int x, int k) {
+        char& f = tri[static_cast<size_t>(k) * p + x];
+        if (f) return;
+        f = 1;
+        out.push_back({GEQRT, x, -1, k, -1});
+        for (int j = k + 1; j < q; ++j) out.push_back({UNMQR, x, -1, k, j});
+    };
+    for (const Elim& e : elims) {
+        factor(e.piv, e.k);
+        if (!ts) factor(e.i, e.k);
+        out.push_back({ts ? TSQRT : TTQRT, e.i, e.piv, e.k, -1});
+        for (int j = e.k + 1; j < q; ++j) out.push_back({ts ? TSMQR : TTMQR, e.i, e.piv, e.k, j});
+    }
+    for (int k = 0; k < std::min(p, q); ++k) factor(k, k);
+}
+
+// Dependencies of tile tasks: the producer of the reflectors a task applies,
+// and the previous writer (in program order) of every tile it writes.
+// Readers of V never delay a writer of the other half of the tile (V: NODEP,
+// T: INPUT, Section 4), hence no write-after-read edges.
+template <class Fn>
+static void for_each_dep(int p, int q, const std::vector<TileTask>& tasks, Fn&& fn) {
+    const size_t nt = static_cast<size_t>(p) * q;
+    std::vector<int64_t> last(nt, -1), prod_ge(nt, -1), prod_el(nt, -1);
+    auto idx = [&](int r, int c) { return static_cast<size_t>(c) * p + r; };
+    int64_t d[4];
+    for (int64_t t = 0; t < static_cast<int64_t>(tasks.size()); ++t) {
+        const TileTask& x = tasks[t];
+        int nd = 0;
+        size_t w[2];
+        int nw = 0;
+        switch (x.kind) {
+            case GEQRT: w[nw++] = idx(x.i, x.k); prod_ge[idx(x.i, x.k)] = t; break;
+            case UNMQR: d[nd++] = prod_ge[idx(x.i, x.k)]; w[nw++] = idx(x.i, x.j); break;
+            case TTQRT:
+            case TSQRT:
+                w[nw++] = idx(x.piv, x.k); w[nw++] = idx(x.i, x.k);
+                prod_el[idx(x.i, x.k)] = t;
+                break;
+            default:  // TTMQR, TSMQR
+                d[nd++] = prod_el[idx(x.i, x.k)];
+                w[nw++] = idx(x.piv, x.j); w[nw++] = idx(x.i, x.j);
+                break;
+        }
+        for (int a = 0; a < nw; ++a) d[nd++] = last[w[a]];
+        for (int a = 0; a < nw; ++a) last[w[a]] = t;
+        fn(t, d, nd);
+    }
+}
+
+int64_t simulate(int p, int q, const std::vector<TileTask>& tasks, std::vector<int64_t>* finish) {
+    std::vector<int64_t> fin(tasks.size(), 0);
+    int64_t cp = 0;
+    for_each_dep(p, q, tasks, [&](int64_t t, const int64_t* d, int nd) {
+        int64_t s = 0;
+        for (int a = 0; a < nd; ++a)
+            if (d[a] >= 0) s = std::max(s, fin[d[a]]);
+        fin[t] = s + kernel_weight(tasks[t].kind);
+        cp = std::max(cp, fin[t]);
+    });
+    if (finish) finish->swap(fin);
+    return cp;
+}
+
+// ---------------------------------------------------------------------------
+// Device task graphs.
+// ---------------------------------------------------------------------------
+static void finish_graph(const std::vector<std::pair<int32_t, int32_t>>& edges, Graph& g) {
+    const size_t nt = g.tasks.size();
+    g.indeg.assign(nt, 0);
+    g.succ_ptr.assign(nt + 1, 0);
+    for (auto& e : edges) { g.succ_ptr[e.first + 1]++; g.indeg[e.second]++; }
+    for (size_t t = 0; t < nt; ++t) g.succ_ptr[t + 1] += g.succ_ptr[t];
+    g.succ.assign(edges.size(), 0);
+    std::vector<int32_t> fill(g.succ_ptr.begin(), g.succ_ptr.end() - 1);
+    for (auto& e : edges) g.succ[fill[e.first]++] = e.second;
+    g.ready.clear();
+    for (size_t t = 0; t < nt; ++t)
+        if (g.indeg[t] == 0) g.ready.push_back(static_cast<int32_t>(t));
+}
+
+// Updates are split into strips of W columns; each strip of a tile has its
+// own chain of writers, while a panel kernel writes all strips of its tiles.
+void build_factor_graph(int p, int q, int nb, int W, int n_cols_last,
+                        const std::vector<TileTask>& tt, Graph& g) {
+    const int smax = (nb + W - 1) / W;
+    auto nstrips = [&](int j) {
+        const int cols = (j == q - 1) ? n_cols_last : nb;
+        return (cols + W - 1) / W;
+    };
+    const size_t ntile = static_cast<size_t>(p) * q;
+    std::vector<int32_t> last(ntile * smax, -1), prod(ntile * 2, -1);
+    auto L = [&](int r, int c, int s) -> int32_t& {
+        return last[(static_cast<size_t>(c) * p + r) * smax + s];
+    };
+    g.tasks.clear();
+    std::vector<std::pair<int32_t, int32_t>> edges;
+    edges.reserve(tt.size() * 4);
+    int32_t deps[2 * 64 + 2];
+    auto add_edges = [&](int32_t t, int nd) {
+        std::sort(deps, deps + nd);
+        for (int a = 0; a < nd; ++a)
+            if (deps[a] >= 0 && (a == 0 || deps[a] != deps[a - 1])) edges.push_back({deps[a], t});
+    };
+    for (const TileTask& x : tt) {
+        if (x.kind == GEQRT || x.kind == TTQRT || x.kind == TSQRT) {
+            const int32_t t = static_cast<int32_t>(g.tasks.size());
+            g.tasks.push_back({x.kind, x.i, x.piv, x.k, -1, 0});
+            int nd = 0;
+            const int rows[2] = {x.i, x.piv};
+            const int nr = (x.kind == GEQRT) ? 1 : 2;
+            for (int a = 0; a < nr; ++a)
+                for (int s = 0; s < nstrips(x.k); ++s) {
+                    deps[nd++] = L(rows[a], x.k, s);
+                    L(rows[a], x.k, s) = t;
+                }
+            add_edges(t, nd);
+            prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == GEQRT ? 0 : 1)] = t;
+        } else {
+            const int32_t pr = prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == UNMQR ? 0 : 1)];
+            for (int s = 0; s < nstrips(x.j); ++s) {
+                const int32_t t = static_cast<int32_t>(g.tasks.size());
+                g.tasks.push_back({x.kind, x.i, x.piv, x.k, x.j, s});
+                int nd = 0;
+                deps[nd++] = pr;
+                deps[nd++] = L(x.i, x.j, s);
+                L(x.i, x.j, s) = t;
+                if (x.kind != UNMQR) {
+                    deps[nd++] = L(x.piv, x.j, s);
+                    L(x.piv, x.j, s) = t;
+                }
+                add_edges(t, nd);
+            }
+        }
+    }
+    finish_graph(edges, g);
+}
+
+void build_apply_graph(int p, const std::vector<TileTask>& tt, int nstrips, bool trans, Graph& g) {
+    std::vector<const TileTask*> panels;
+    for (const TileTask& x : tt)
+        if (x.kind == GEQRT || x.kind == TTQRT || x.kind == TSQRT) panels.push_back(&x);
+    if (!trans) std::reverse(panels.begin(), panels.end());
+    std::vector<int32_t> last(static_cast<size_t>(p) * nstrips, -1);
+    g.tasks.clear();
+    std::vector<std::pair<int32_t, int32_t>> edges;
+    for (const TileTask* x : panels) {
+        const int kind = (x->kind == GEQRT) ? UNMQR : (x->kind == TTQRT ? TTMQR : TSMQR);
+        for (int s = 0; s < nstrips; ++s) {
+            const int32_t t = static_cast<int32_t>(g.tasks.size());
+            g.tasks.push_back({kind, x->i, x->piv, x->k, -1, s});
+            int32_t& a = last[static_cast<size_t>(x->i) * nstrips + s];
+            if (a >= 0) edges.push_back({a, t});
+            a = t;
+            if (kind != UNMQR) {
+                int32_t& b = last[static_cast<size_t>(x->piv) * nstrips + s];
+                if (b >= 0) edges.push_back({b, t});
+                b = t;
+            }
+        }
+    }
+    finish_graph(edges, g);
+}
+
+}  // namespace tqr

@@ -1,0 +1,114 @@
+// Internal declarations shared by the host planner, the device executor and
+// the C ABI of libtqr.  Not installed; the public interface is include/tqr.h.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+#include <memory>
+#include <cuda_runtime.h>
+
+namespace tqr {
+
+// Kernel kinds (same numbering as tqr_kernel in tqr.h).
+enum Kind : int32_t { GEQRT = 0, UNMQR = 1, TTQRT = 2, TTMQR = 3, TSQRT = 4, TSMQR = 5 };
+
+// Table 1 of the paper: cost of each kernel in units of nb^3/3 flops.
+inline int kernel_weight(int kind) {
+    static const int w[6] = {4, 6, 2, 6, 6, 12};
+    return w[kind];
+}
+
+struct Elim { int32_t i, piv, k; };                 // 0-based elim(i, piv, k)
+struct TileTask { int32_t kind, i, piv, k, j; };     // 0-based; piv/j = -1 when unused
+
+// One device task.  Update kernels are split into column strips: `strip`
+// selects columns [strip*W, strip*W + W) of tile column j (or of B).
+struct DevTask {
+    int32_t kind;    // Kind
+    int32_t i;       // row of the tile factored / zeroed / updated
+    int32_t piv;     // pivot row (TT/TS kernels), else -1
+    int32_t k;       // panel column
+    int32_t j;       // update column (updates), else -1
+    int32_t strip;   // column strip (updates), else 0
+};
+
+// ---- host planner (planner.cpp) ----
+int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out);
+int validate_elims(int p, int q, const Elim* e, int64_t count);
+void expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out);
+// Unit-weight ASAP finish time of every tile task and the critical path.
+int64_t simulate(int p, int q, const std::vector<TileTask>& tasks, std::vector<int64_t>* finish);
+
+// Device task graph: tasks, successor lists (CSR) and in-degrees.
+struct Graph {
+    std::vector<DevTask> tasks;
+    std::vector<int32_t> succ_ptr;   // size ntasks+1
+    std::vector<int32_t> succ;
+    std::vector<int32_t> indeg;
+    std::vector<int32_t> ready;      // tasks with in-degree 0, program order
+};
+
+// Graph of the factorization: updates split into strips of W columns.
+// n_cols_last: number of valid columns of the last tile column.
+void build_factor_graph(int p, int q, int nb, int W, int n_cols_last,
+                        const std::vector<TileTask>& tt, Graph& g);
+// Graph replaying the panel tasks' transformations on a right-hand side of
+// nstrips strips (trans = Q^T order, else reverse order for Q).
+void build_apply_graph(int p, const std::vector<TileTask>& tt, int nstrips, bool trans, Graph& g);
+
+}  // namespace tqr
+
+// ---------------------------------------------------------------------------
+// Device side (device.cu).
+// ---------------------------------------------------------------------------
+namespace tqr {
+
+constexpr int kThreads = 256;   // threads per executor CTA
+
+// A task graph resident in device memory (immutable after upload).
+struct DevGraph {
+    DevTask* tasks = nullptr;
+    int32_t* succ_ptr = nullptr;
+    int32_t* succ = nullptr;
+    int32_t* indeg = nullptr;
+    int32_t* ready = nullptr;
+    int32_t ntasks = 0, nready = 0;
+    int64_t nedges = 0;
+};
+
+// Mutable per-run state of the executor: dependency counters, ready queue,
+// queue head/tail and the status word.
+struct ExecState {
+    int32_t* deps = nullptr;
+    int32_t* queue = nullptr;
+    uint32_t* ctr = nullptr;     // [0] head, [1] tail
+    int32_t* status = nullptr;
+    int32_t capacity = 0;        // tasks the arrays can hold
+};
+
+// Everything one executor launch needs (passed by value as a kernel argument).
+struct ExecParams {
+    double* A; int64_t lda; int64_t m, n;       // matrix being factored (R and V)
+    int nb, ib, p, q;
+    double* tau_ge;                              // tau of GEQRT(i,k): [(k*p+i)*nb + r]
+    double* tau_el;                              // tau of TTQRT/TSQRT zeroing (i,k)
+    double* B; int64_t ldb, nrhs;                // right-hand side (apply graphs), else null
+    int trans;                                   // 1: apply Q^T, 0: apply Q
+    const DevTask* tasks; const int32_t* succ_ptr; const int32_t* succ;
+    int32_t* deps; int32_t* queue; uint32_t* ctr; int32_t* status;
+    int32_t ntasks;
+    uint64_t timeout_ns;                         // limit for any single wait
+};
+
+// Row groups per strip column (G) and dynamic shared memory for (nb, ib);
+// returns false if no layout fits.
+bool choose_layout(int nb, int ib, int* G, int* smem_bytes);
+int strip_width(int G);
+int device_sm_count();
+cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,
+                               int smem, bool reset_status, cudaStream_t s);
+// T factors of the listed panel tasks (kind, i, k triplets on the device).
+cudaError_t launch_form_t(const ExecParams& P, const int32_t* panels, int npanels,
+                          double* T_ge, double* T_el, cudaStream_t s);
+
+}  // namespace tqr

@@ -1,0 +1,291 @@
+"""Python binding of libtqr (include/tqr.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Matrices are
+torch tensors on the GPU holding FP64 data in column-major order, i.e. a
+tensor ``A`` of shape (m, n) with ``A.stride() == (1, m)`` (see
+:func:`colmajor`).  Device work is enqueued on the current torch stream unless
+a stream is given.  Errors raise :class:`TqrError`; the library must be built
+(``paper_1104_4475_gb300.build.build()``) -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+GEQRT, UNMQR, TTQRT, TTMQR, TSQRT, TSMQR = range(6)
+FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA = range(7)
+TREES = {"flat_ts": FLAT_TS, "flat_tt": FLAT_TT, "sameh_kuck": SAMEH_KUCK, "binary": BINARY,
+         "fibonacci": FIBONACCI, "greedy": GREEDY, "plasma": PLASMA}
+
+TQR_ERR_INVALID_LIST = -100
+TQR_ERR_TIMEOUT = -101
+TQR_ERR_NONFINITE = -102
+TQR_ERR_CUDA = -103
+TQR_ERR_NOMEM = -104
+TQR_ERR_CAPACITY = -105
+
+
+class TqrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, tqr_strerror(code), code))
+
+
+class tqr_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("tree", ctypes.c_int32), ("BS", ctypes.c_int32),
+                ("ts", ctypes.c_int32), ("strip", ctypes.c_int32), ("n_elims", ctypes.c_int64),
+                ("n_tile_tasks", ctypes.c_int64), ("n_device_tasks", ctypes.c_int64),
+                ("n_edges", ctypes.c_int64), ("critical_path", ctypes.c_int64), ("flops", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libtqr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libtqr.so is not built (run paper_1104_4475_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        pi32, pi64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "tqr_factor": [vp, i64, i64, i32, i32, i32, i32, vp, ctypes.POINTER(vp)],
+            "tqr_factor_list": [vp, i64, i64, i32, i32, pi32, i64, i32, vp, ctypes.POINTER(vp)],
+            "tqr_apply_qt": [vp, vp, i64, i64, vp],
+            "tqr_apply_q": [vp, vp, i64, i64, vp],
+            "tqr_form_t": [vp, vp, vp, vp],
+            "tqr_sync": [vp],
+            "tqr_get_info": [vp, ctypes.POINTER(tqr_info)],
+            "tqr_factor_host": [vp, i64, i64, i32, i32, i32, i32, vp, i64, vp, ctypes.POINTER(vp)],
+            "tqr_elimination_list": [i32, i32, i32, i32, pi32, i64, pi64],
+            "tqr_validate_list": [i32, i32, pi32, i64],
+            "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
+            "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.tqr_set_timeout_ms.argtypes = [ctypes.c_double]
+        L.tqr_set_timeout_ms.restype = ctypes.c_int
+        L.tqr_inject_fault.argtypes = [ctypes.c_int]
+        L.tqr_inject_fault.restype = ctypes.c_int
+        L.tqr_free.argtypes = [vp]
+        L.tqr_free.restype = None
+        L.tqr_strerror.argtypes = [ctypes.c_int]
+        L.tqr_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise TqrError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _colmajor_ptr(t, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError("%s must be a 2-D float64 CUDA tensor" % what)
+    m = t.shape[0]
+    if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) < m):
+        raise ValueError("%s must be column-major (stride (1, ld) with ld >= rows)" % what)
+    return ctypes.c_void_p(t.data_ptr()), (t.stride(1) if t.shape[1] > 1 else max(1, m))
+
+
+def colmajor(x, device="cuda"):
+    """A column-major float64 CUDA tensor holding the 2-D array ``x``."""
+    import torch
+    a = np.asarray(x, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()
+
+
+def to_numpy(t):
+    """A numpy copy of a (column-major) tensor."""
+    return t.detach().cpu().numpy().copy()
+
+
+class Factors:
+    """A tqr_factors handle (owns the library-side state of one factorization)."""
+
+    def __init__(self, ptr, A):
+        self.ptr = ptr
+        self.A = A
+
+    def info(self):
+        return tqr_get_info(self)
+
+    def free(self):
+        if self.ptr:
+            lib().tqr_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------- device
+def tqr_factor(A, nb, ib, tree, BS=1, stream=None, reuse=None):
+    """QR of the column-major CUDA tensor A in place (R and V); returns a
+    Factors handle.  ``reuse`` (a Factors of the same shape and parameters)
+    makes the call allocate nothing."""
+    ptr, ld = _colmajor_ptr(A, "A")
+    m, n = A.shape
+    if ld != m:
+        raise ValueError("A must have leading dimension m")
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    _check(lib().tqr_factor(ptr, m, n, nb, ib, int(tree), BS, _stream(stream), ctypes.byref(h)), "tqr_factor")
+    if reuse is not None and h.value == reuse.ptr:
+        reuse.A = A
+        return reuse
+    return Factors(h.value, A)
+
+
+def tqr_factor_list(A, nb, ib, elims, ts=False, stream=None, reuse=None):
+    """QR with a caller-given elimination list of 0-based (i, piv, k)."""
+    ptr, ld = _colmajor_ptr(A, "A")
+    m, n = A.shape
+    arr = np.ascontiguousarray(np.asarray(elims, dtype=np.int32).reshape(-1, 3))
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    rc = lib().tqr_factor_list(ptr, m, n, nb, ib, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               arr.shape[0], 1 if ts else 0, _stream(stream), ctypes.byref(h))
+    _check(rc, "tqr_factor_list")
+    if reuse is not None and h.value == reuse.ptr:
+        reuse.A = A
+        return reuse
+    return Factors(h.value, A)
+
+
+def tqr_apply_qt(f, B, stream=None):
+    """B <- Q^T B in place (B: column-major CUDA tensor with m rows)."""
+    ptr, ld = _colmajor_ptr(B, "B")
+    _check(lib().tqr_apply_qt(ctypes.c_void_p(f.ptr), ptr, ld, B.shape[1], _stream(stream)), "tqr_apply_qt")
+    return B
+
+
+def tqr_apply_q(f, B, stream=None):
+    """B <- Q B in place."""
+    ptr, ld = _colmajor_ptr(B, "B")
+    _check(lib().tqr_apply_q(ctypes.c_void_p(f.ptr), ptr, ld, B.shape[1], _stream(stream)), "tqr_apply_q")
+    return B
+
+
+def tqr_form_t(f, T_geqrt=None, T_elim=None, stream=None):
+    """Fill the T factor arrays (CUDA float64 tensors of p*q*ib*nb elements)."""
+    def p(t):
+        return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+    _check(lib().tqr_form_t(ctypes.c_void_p(f.ptr), p(T_geqrt), p(T_elim), _stream(stream)), "tqr_form_t")
+
+
+def tqr_sync(f, raise_on_error=True):
+    rc = lib().tqr_sync(ctypes.c_void_p(f.ptr))
+    if raise_on_error:
+        _check(rc, "tqr_sync")
+    return rc
+
+
+def tqr_get_info(f):
+    info = tqr_info()
+    _check(lib().tqr_get_info(ctypes.c_void_p(f.ptr), ctypes.byref(info)), "tqr_get_info")
+    return {k: getattr(info, k) for k, _ in tqr_info._fields_}
+
+
+def tqr_free(f):
+    f.free()
+
+
+def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None):
+    """End to end on host arrays: A (m x n, Fortran-ordered float64 numpy
+    array) is overwritten by R and V; B (m x nrhs, Fortran order) by Q^T B."""
+    if not (isinstance(A, np.ndarray) and A.dtype == np.float64 and A.flags.f_contiguous):
+        raise TypeError("A must be a Fortran-ordered float64 numpy array")
+    m, n = A.shape
+    bp, nrhs = None, 0
+    if B is not None:
+        if not (isinstance(B, np.ndarray) and B.dtype == np.float64 and B.flags.f_contiguous and B.shape[0] == m):
+            raise TypeError("B must be a Fortran-ordered float64 numpy array with m rows")
+        bp, nrhs = ctypes.c_void_p(B.ctypes.data), (B.shape[1] if B.ndim == 2 else 1)
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    rc = lib().tqr_factor_host(ctypes.c_void_p(A.ctypes.data), m, n, nb, ib, int(tree), BS, bp, nrhs,
+                               _stream(stream), ctypes.byref(h))
+    _check(rc, "tqr_factor_host")
+    if reuse is not None and h.value == reuse.ptr:
+        return reuse
+    return Factors(h.value, None)
+
+
+# ---------------------------------------------------------------- host only
+def tqr_elimination_list(p, q, tree, BS=1):
+    """0-based (i, piv, k) triplets as an (count, 3) int32 array."""
+    cnt = ctypes.c_int64(0)
+    rc = lib().tqr_elimination_list(p, q, int(tree), BS, None, 0, ctypes.byref(cnt))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_elimination_list")
+    out = np.zeros((max(1, cnt.value), 3), dtype=np.int32)
+    _check(lib().tqr_elimination_list(p, q, int(tree), BS, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      out.shape[0], ctypes.byref(cnt)), "tqr_elimination_list")
+    return out[: cnt.value]
+
+
+def tqr_validate_list(p, q, elims):
+    arr = np.ascontiguousarray(np.asarray(elims, dtype=np.int32).reshape(-1, 3))
+    return lib().tqr_validate_list(p, q, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), arr.shape[0])
+
+
+def tqr_critical_path(p, q, tree, BS=1, zero_time=False):
+    cp = ctypes.c_int64(0)
+    zt = np.zeros(p * q, dtype=np.int32) if zero_time else None
+    zp = zt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if zero_time else None
+    _check(lib().tqr_critical_path(p, q, int(tree), BS, ctypes.byref(cp), zp), "tqr_critical_path")
+    if zero_time:
+        return cp.value, zt.reshape(p, q)
+    return cp.value
+
+
+def tqr_tasks(p, q, tree, BS=1):
+    """(tasks (count, 5) int32: kind, i, piv, k, j; finish (count,) int64)."""
+    cnt = ctypes.c_int64(0)
+    rc = lib().tqr_tasks(p, q, int(tree), BS, None, None, 0, ctypes.byref(cnt))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_tasks")
+    out = np.zeros((max(1, cnt.value), 5), dtype=np.int32)
+    fin = np.zeros(max(1, cnt.value), dtype=np.int64)
+    _check(lib().tqr_tasks(p, q, int(tree), BS, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), out.shape[0], ctypes.byref(cnt)),
+           "tqr_tasks")
+    return out[: cnt.value], fin[: cnt.value]
+
+
+def tqr_set_timeout_ms(ms):
+    _check(lib().tqr_set_timeout_ms(float(ms)), "tqr_set_timeout_ms")
+
+
+def tqr_inject_fault(kind):
+    _check(lib().tqr_inject_fault(int(kind)), "tqr_inject_fault")
+
+
+def tqr_strerror(code):
+    return lib().tqr_strerror(int(code)).decode()

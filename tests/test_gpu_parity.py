@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Element-wise tolerance.  The library and the oracle run the same reflectors
+in the same order but sum dot products in a different order, so each result
+is a backward-stable QR of A with its own rounding.  Perturbation theory of
+QR bounds the difference of two such R (and of the reflectors, whose entries
+are at most 1 in magnitude) by about kappa(A) * m * u * ||A||; the tests take
+TOL * max|R| with TOL = 8 * kappa(A) * m * u (u = 2^-53), floored at 1e-13.
+Independently of the oracle, every GPU result must meet the absolute targets
+||A - QR||_F / ||A||_F <= 1e-13 and ||I - Q^T Q||_F <= 1e-13.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import FLAT_TS as O_FLAT_TS
+from oracle import tiled_qr as otq
+from oracle import trees as otrees
+import paper_1104_4475_gb300 as tqr
+from paper_1104_4475_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4475_gb300 import build
+    build.build()
+    tqr.tqr_set_timeout_ms(0)
+
+
+def tol_for(A):
+    kappa = np.linalg.cond(A)
+    return max(1e-13, 8 * kappa * A.shape[0] * U)
+
+
+def gpu_factor(A, nb, ib, tree, BS=1):
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, nb, ib, tree, BS)
+    tqr.tqr_sync(f)
+    return f, tqr.to_numpy(At)
+
+
+def gpu_q_explicit(f, m, n):
+    E = np.zeros((m, n))
+    E[:n, :n] = np.eye(n)
+    Et = tqr.colmajor(E)
+    tqr.tqr_apply_q(f, Et)
+    tqr.tqr_sync(f)
+    return tqr.to_numpy(Et)
+
+
+def check_targets(f, A, Aout):
+    m, n = A.shape
+    R = np.triu(Aout[:n, :n])
+    Q = gpu_q_explicit(f, m, n)
+    res = np.linalg.norm(A - Q @ R) / np.linalg.norm(A)
+    orth = np.linalg.norm(np.eye(n) - Q.T @ Q)
+    assert res <= 1e-13, res
+    assert orth <= 1e-13, orth
+    return Q, R
+
+
+def compare(gpu, ref, scale, tol, what):
+    err = np.abs(gpu - ref).max() / scale
+    assert err <= tol, "%s: %.3e > %.3e" % (what, err, tol)
+    return err
+
+
+def test_small_config_parity():
+    """1024 x 256, nb 64, ib 16, Greedy, N(0,1): R, V, T, Q^T b against the
+    oracle; residual and orthogonality targets."""
+    A, b = workloads.small_config(0)
+    f, Aout = gpu_factor(A, 64, 16, tqr.GREEDY)
+    F = otq.factor(A, 64, 16, tqr.GREEDY)
+    tol = tol_for(A)
+    scale = np.abs(F.r()).max()
+    compare(Aout, F.A, scale, tol, "R and V")
+    info = f.info()
+    assert info["p"] == 16 and info["q"] == 4 and info["n_elims"] == 54 and info["critical_path"] == 86
+    # T factors formed from the stored reflectors.
+    p, q, ib, nb = 16, 4, 16, 64
+    Tge = torch.zeros(p * q * ib * nb, dtype=torch.float64, device="cuda")
+    Tel = torch.zeros_like(Tge)
+    tqr.tqr_form_t(f, Tge, Tel)
+    tqr.tqr_sync(f)
+    Tge = Tge.cpu().numpy().reshape(q, p, nb, ib).transpose(1, 0, 3, 2)
+    Tel = Tel.cpu().numpy().reshape(q, p, nb, ib).transpose(1, 0, 3, 2)
+    compare(Tge, F.Tge, 1.0, tol, "T of GEQRT")
+    compare(Tel, F.Tel, 1.0, tol, "T of TTQRT")
+    # Q^T b
+    bt = tqr.colmajor(b)
+    tqr.tqr_apply_qt(f, bt)
+    tqr.tqr_sync(f)
+    compare(tqr.to_numpy(bt)[:, 0], otq.apply_qt(F, b), np.linalg.norm(b), tol, "Q^T b")
+    check_targets(f, A, Aout)
+    f.free()
+
+
+TREES = [(tqr.FLAT_TS, 1), (tqr.FLAT_TT, 1), (tqr.SAMEH_KUCK, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1),
+         (tqr.GREEDY, 1), (tqr.PLASMA, 1), (tqr.PLASMA, 3), (tqr.PLASMA, 10)]
+
+
+@pytest.mark.parametrize("tree,BS", TREES)
+def test_every_tree_ragged(tree, BS):
+    """300 x 130, nb 32, ib 8: 10 x 5 tiles with a ragged last tile row and
+    column, uniform entries."""
+    A = workloads.uniform(300, 130, seed=tree * 10 + BS)
+    f, Aout = gpu_factor(A, 32, 8, tree, BS)
+    F = otq.factor(A, 32, 8, tree, BS)
+    compare(Aout, F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
+    check_targets(f, A, Aout)
+    f.free()
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", [
+    (64, 64, 64, 16, tqr.GREEDY),       # one tile
+    (50, 30, 64, 16, tqr.GREEDY),       # one partial tile
+    (40, 40, 16, 4, tqr.FLAT_TT),       # ragged square
+    (512, 512, 64, 8, tqr.GREEDY),      # square, p = q
+    (512, 512, 64, 8, tqr.FLAT_TS),
+    (1000, 64, 64, 32, tqr.FIBONACCI),  # q = 1
+    (1000, 64, 64, 64, tqr.BINARY),     # ib = nb
+    (1536, 512, 256, 32, tqr.GREEDY),   # nb 256: four strips per tile column
+    (2000, 700, 256, 32, tqr.FLAT_TS),  # nb 256, ragged
+    (700, 300, 48, 16, tqr.GREEDY),     # nb not a power of two
+])
+def test_shapes(m, n, nb, ib, tree):
+    A = workloads.gaussian(m, n, seed=m + n)
+    f, Aout = gpu_factor(A, nb, ib, tree)
+    F = otq.factor(A, nb, ib, tree)
+    compare(Aout, F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
+    check_targets(f, A, Aout)
+    f.free()
+
+
+def test_apply_roundtrip_and_multiple_rhs():
+    A = workloads.gaussian(640, 320, seed=3)
+    f, Aout = gpu_factor(A, 64, 16, tqr.GREEDY)
+    F = otq.factor(A, 64, 16, tqr.GREEDY)
+    B = workloads.rhs(640, 70, seed=4)                 # 70 columns: two strips, ragged
+    Bt = tqr.colmajor(B)
+    tqr.tqr_apply_qt(f, Bt)
+    tqr.tqr_sync(f)
+    QtB = tqr.to_numpy(Bt)
+    compare(QtB, otq.apply_qt(F, B), np.abs(B).max(), tol_for(A), "Q^T B")
+    tqr.tqr_apply_q(f, Bt)
+    tqr.tqr_sync(f)
+    compare(tqr.to_numpy(Bt), B, np.abs(B).max(), 1e-13, "Q Q^T B")
+    f.free()
+
+
+def test_caller_given_list():
+    """A random valid elimination list (neither tree's) through tqr_factor_list."""
+    rng = np.random.default_rng(9)
+    p, q, nb, ib = 9, 4, 32, 8
+    zeroed, el = set(), []
+    while len(el) < sum(p - k for k in range(1, q + 1)):
+        cands = []
+        for k in range(1, q + 1):
+            for i in range(k + 1, p + 1):
+                if (i, k) in zeroed or any((i, kp) not in zeroed for kp in range(1, k)):
+                    continue
+                pivs = [r for r in range(k, i) if (r, k) not in zeroed
+                        and all((r, kp) in zeroed for kp in range(1, k))]
+                cands += [(i, r, k) for r in pivs]
+        e = cands[rng.integers(len(cands))]
+        el.append(e)
+        zeroed.add((e[0], e[2]))
+    assert otrees.validate(p, q, el) is None
+    A = workloads.gaussian(p * nb - 5, q * nb - 3, seed=5)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor_list(At, nb, ib, np.array(el) - 1)
+    tqr.tqr_sync(f)
+    F = otq.factor(A, nb, ib, tqr.GREEDY, elims=el)
+    compare(tqr.to_numpy(At), F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
+    bad = list(el)
+    bad[0], bad[-1] = bad[-1], bad[0]
+    with pytest.raises(tqr.TqrError) as e:
+        tqr.tqr_factor_list(tqr.colmajor(A), nb, ib, np.array(bad) - 1)
+    assert e.value.code == tqr.TQR_ERR_INVALID_LIST
+    f.free()
+
+
+def test_reuse_allocates_nothing_and_repeats():
+    A = workloads.gaussian(512, 256, seed=6)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
+    tqr.tqr_sync(f)
+    first = tqr.to_numpy(At)
+    At2 = tqr.colmajor(A)
+    g = tqr.tqr_factor(At2, 64, 16, tqr.GREEDY, reuse=f)
+    assert g is f
+    tqr.tqr_sync(g)
+    assert np.array_equal(tqr.to_numpy(At2), first)   # the executor is deterministic per task
+    f.free()
+
+
+def test_host_end_to_end():
+    A = np.asfortranarray(workloads.gaussian(768, 256, seed=7))
+    b = np.asfortranarray(workloads.rhs(768, 1, seed=8))
+    Ah, bh = A.copy(order="F"), b.copy(order="F")
+    f = tqr.tqr_factor_host(Ah, 64, 16, tqr.GREEDY, B=bh)
+    F = otq.factor(A, 64, 16, tqr.GREEDY)
+    compare(Ah, F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
+    compare(bh[:, 0], otq.apply_qt(F, b[:, 0]), np.linalg.norm(b), tol_for(A), "Q^T b")
+    f.free()
+
+
+def test_nonfinite_input_reports_status():
+    A = workloads.gaussian(256, 128, seed=1)
+    A[17, 3] = np.nan
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
+    assert tqr.tqr_sync(f, raise_on_error=False) == tqr.TQR_ERR_NONFINITE
+    f.free()
+
+
+def test_timeout_is_reported_and_context_survives():
+    """Failure detection without a GPU fault: the host drops the ready tasks,
+    every device wait runs out after 500 ms, the status says so, and the next
+    factorization on the same context is correct."""
+    A = workloads.gaussian(256, 128, seed=2)
+    tqr.tqr_set_timeout_ms(500)
+    try:
+        tqr.tqr_inject_fault(1)
+        At = tqr.colmajor(A)
+        f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
+        assert tqr.tqr_sync(f, raise_on_error=False) == tqr.TQR_ERR_TIMEOUT
+        f.free()
+    finally:
+        tqr.tqr_set_timeout_ms(0)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
+    tqr.tqr_sync(f)
+    F = otq.factor(A, 64, 16, tqr.GREEDY)
+    compare(tqr.to_numpy(At), F.A, np.abs(F.r()).max(), tol_for(A), "R and V after timeout")
+    f.free()

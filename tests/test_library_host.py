@@ -1,0 +1,135 @@
+"""libtqr on the CPU: the library loads, exports every entry point of
+include/tqr.h, and its host-only integer outputs (elimination lists,
+validity verdicts, task lists, unit-weight schedules, critical paths,
+zero-out tables) equal the oracle's bit for bit."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import dag as odag
+from oracle import trees as otrees
+import paper_1104_4475_gb300 as tqr
+from paper_1104_4475_gb300 import build as tbuild
+
+KIND_MAP = {odag.GEQRT: tqr.GEQRT, odag.UNMQR: tqr.UNMQR, odag.TTQRT: tqr.TTQRT,
+            odag.TTMQR: tqr.TTMQR, odag.TSQRT: tqr.TSQRT, odag.TSMQR: tqr.TSMQR}
+TREES = [tqr.FLAT_TS, tqr.FLAT_TT, tqr.SAMEH_KUCK, tqr.BINARY, tqr.FIBONACCI, tqr.GREEDY]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tbuild.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "tqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tqr_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = header_functions()
+    assert len(names) >= 14
+    L = tqr.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    out = os.popen("nm -D --defined-only %s" % tbuild.LIB).read()
+    for name in names:
+        assert re.search(r"\bT %s$" % name, out, flags=re.M), name
+
+
+def test_library_is_built_for_sm103a():
+    out = os.popen("cuobjdump --list-elf %s 2>/dev/null" % tbuild.LIB).read()
+    if out:
+        assert "sm_103a" in out
+
+
+def lists_equal(p, q, tree, BS=1):
+    got = tqr.tqr_elimination_list(p, q, tree, BS)
+    want = np.array(otrees.elimination_list(p, q, tree, BS), dtype=np.int32).reshape(-1, 3) - 1
+    return got.shape == want.shape and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("tree", TREES)
+def test_elimination_lists_match_oracle(tree):
+    for p in range(1, 34):
+        for q in range(1, p + 1):
+            assert lists_equal(p, q, tree), (p, q)
+
+
+def test_plasma_lists_match_oracle():
+    for p in range(1, 26):
+        for q in range(1, p + 1):
+            for BS in range(1, p + 1):
+                assert lists_equal(p, q, tqr.PLASMA, BS), (p, q, BS)
+
+
+@pytest.mark.parametrize("p,q,tree,BS", [(16, 4, tqr.GREEDY, 1), (15, 6, tqr.FIBONACCI, 1), (40, 17, tqr.PLASMA, 7),
+                                         (64, 64, tqr.GREEDY, 1), (64, 8, tqr.FLAT_TS, 1), (33, 20, tqr.BINARY, 1),
+                                         (9, 9, tqr.FLAT_TT, 1), (1, 1, tqr.GREEDY, 1), (7, 1, tqr.FLAT_TS, 1)])
+def test_tasks_schedule_and_cp_match_oracle(p, q, tree, BS):
+    el = otrees.elimination_list(p, q, tree, BS)
+    ts = tree == tqr.FLAT_TS
+    otasks = odag.expand(p, q, el, ts)
+    ofin, ocp = odag.simulate(otasks)
+    tasks, fin = tqr.tqr_tasks(p, q, tree, BS)
+    want = np.array([[KIND_MAP[k], i - 1, piv - 1 if piv else -1, kk - 1, j - 1 if j else -1]
+                     for (k, i, piv, kk, j) in otasks], dtype=np.int32).reshape(-1, 5)
+    assert np.array_equal(tasks, want)
+    assert np.array_equal(fin, np.array(ofin, dtype=np.int64))
+    cp, zt = tqr.tqr_critical_path(p, q, tree, BS, zero_time=True)
+    assert cp == ocp
+    ozt = odag.zero_times(otasks, ofin)
+    for i in range(p):
+        for k in range(q):
+            assert zt[i, k] == ozt.get((i + 1, k + 1), -1)
+
+
+def test_critical_paths_sweep_match_oracle():
+    for p in (2, 5, 16, 40):
+        for q in range(1, p + 1, 3):
+            for tree in TREES:
+                el = otrees.elimination_list(p, q, tree)
+                assert tqr.tqr_critical_path(p, q, tree) == odag.critical_path(p, q, el, tree == tqr.FLAT_TS)
+
+
+def test_validator_agrees_with_oracle():
+    rng = np.random.default_rng(0)
+    p, q = 7, 3
+    good = otrees.greedy(p, q)
+    assert tqr.tqr_validate_list(p, q, np.array(good) - 1) == 0
+    agree = 0
+    for trial in range(400):
+        el = [list(e) for e in good]
+        kind = trial % 4
+        if kind == 0:                                     # swap two entries
+            a, b = rng.integers(0, len(el), 2)
+            el[a], el[b] = el[b], el[a]
+        elif kind == 1:                                   # change a pivot
+            a = rng.integers(0, len(el))
+            el[a][1] = int(rng.integers(el[a][2], p + 1))
+        elif kind == 2:                                   # drop an entry
+            del el[rng.integers(0, len(el))]
+        else:                                             # duplicate an entry
+            el.append(list(el[rng.integers(0, len(el))]))
+        ok_oracle = otrees.validate(p, q, [tuple(e) for e in el]) is None
+        rc = tqr.tqr_validate_list(p, q, np.array(el, dtype=np.int32) - 1)
+        assert (rc == 0) == ok_oracle, el
+        agree += 1
+    assert agree == 400
+
+
+def test_argument_errors():
+    L = tqr.lib()
+    assert L.tqr_critical_path(0, 1, 5, 1, None, None) == -1
+    cp = np.zeros(1, dtype=np.int64)
+    assert tqr.lib().tqr_critical_path(4, 5, 5, 1, cp.ctypes.data_as(tqr.tqr.ctypes.POINTER(tqr.tqr.ctypes.c_int64)),
+                                       None) == -2
+    assert tqr.lib().tqr_elimination_list(8, 2, 6, 0, None, 0, None) == -4
+    with pytest.raises(tqr.TqrError):
+        tqr.tqr_critical_path(4, 2, 99)
+    assert tqr.tqr_strerror(tqr.TQR_ERR_TIMEOUT) == "device wait timed out"
