@@ -1,0 +1,353 @@
+"""Benchmark: FP64 tiled QR GFLOP/s on GB300 (libtqr, C ABI).
+
+Workload ("tree sweep"): m = 16384 (p = 64 tile rows), nb = 256, ib = 32,
+n = 256 q for q in {1, 2, 4, 8, 16, 32, 64}, entries iid U[-0.5, 0.5]
+(seed 1), Greedy tree (TT kernels).  One step factors all seven matrices;
+flops = sum of 2 n^2 (m - n/3) (the LAPACK count).  Inputs are resident in
+HBM; each step first restores the seven matrices from pristine copies
+(device-to-device, 8.5 GB of traffic) after writing a 256 MiB buffer to
+flush L2, and both are inside the timed region.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (numpy, the machine's host cores) on a bounded sample of the same
+workload.  ``--gpus N`` under torchrun runs N independent replicas (the
+factorization of one matrix does not shard), reported as weak scaling.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, NB, IB = 16384, 256, 32
+QS = (1, 2, 4, 8, 16, 32, 64)
+TREE_NAME = "Greedy"
+SEED = 1
+# FP64 peak from unit counts: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2.070 GHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+CPU_SAMPLE_QS = (1, 2)
+
+
+def flops(m, n):
+    return 2.0 * n * n * (m - n / 3.0)
+
+
+def workload_flops(qs=QS):
+    return sum(flops(M, NB * q) for q in qs)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle (CPU)
+def oracle_sample(qs=CPU_SAMPLE_QS):
+    """Time the CPU oracle on complete factorizations of the sweep points qs."""
+    from oracle import tiled_qr as otq
+    from paper_1104_4475_gb300 import workloads
+    fl, t = 0.0, 0.0
+    for q in qs:
+        A = workloads.uniform(M, NB * q, SEED)
+        t0 = time.perf_counter()
+        otq.factor(A, NB, IB, 5)
+        t += time.perf_counter() - t0
+        fl += flops(M, NB * q)
+    return fl, t
+
+
+def run_oracle_subprocess(steps=1):
+    """The oracle in a fresh process (spawned, before/independent of CUDA) with
+    its BLAS threads set to the host's core count.  Returns (gflops, cores)."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = [bench.oracle_sample() for _ in range(%d)]; print(json.dumps(r))" % (ROOT, steps))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1]), cores
+
+
+def sample_desc():
+    return ("complete CPU-oracle factorizations of the q in %s points of the sweep (m=%d, nb=%d, ib=%d, Greedy), "
+            "%.3g flop" % (list(CPU_SAMPLE_QS), M, NB, IB, workload_flops(CPU_SAMPLE_QS)))
+
+
+def reference_main(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    res, cores = run_oracle_subprocess(args.warmup + args.steps)
+    timed = res[args.warmup:]
+    fl = sum(r[0] for r in timed)
+    t = sum(r[1] for r in timed)
+    value = fl / t / 1e9
+    line = {
+        "impl": "reference", "metric": "tiled-QR GFLOP/s (FP64)", "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc()},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict():
+    return {"workload": "FP64 tree sweep: m=16384 (p=64), nb=256, ib=32, n=256q for q in "
+                        "{1,2,4,8,16,32,64}, U[-0.5,0.5] entries, Greedy tree (TT kernels)",
+            "m": M, "nb": NB, "ib": IB, "q": list(QS), "tree": TREE_NAME, "parallelism": "replicas",
+            "l2": "256 MiB flush write + input restore (8.5 GB D2D) each step, inside the timed region"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def gpu_main(args):
+    import torch
+    import paper_1104_4475_gb300 as tqr
+    from paper_1104_4475_gb300 import build, workloads
+
+    rank, world, local = dist_env()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res, cores = run_oracle_subprocess(1)        # before any CUDA call
+        cpu = {"value": res[0][0] / res[0][1] / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": sample_desc()}
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+
+    # Inputs resident in HBM: pristine copies and working buffers.
+    pristine, work = {}, {}
+    for q in QS:
+        a = workloads.uniform(M, NB * q, SEED)
+        pristine[q] = torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+        work[q] = torch.empty_like(pristine[q].t()).t()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    handles = {}
+    launches = 0
+
+    def step(kernel_times=None):
+        nonlocal launches
+        flush.fill_(1.0)
+        for q in QS:
+            work[q].copy_(pristine[q])
+        for q in QS:
+            if kernel_times is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            handles[q] = tqr.tqr_factor(work[q], NB, IB, tqr.GREEDY, 1, stream=stream, reuse=handles.get(q))
+            launches += 2                               # init + executor
+            if kernel_times is not None:
+                e1.record(stream)
+                kernel_times.append((q, e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for q in QS:
+        tqr.tqr_sync(handles[q])
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    kt = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(kt)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    for q in QS:
+        rc = tqr.tqr_sync(handles[q], raise_on_error=False)
+        if rc != 0:
+            raise RuntimeError("device status %d (%s) at q=%d" % (rc, tqr.tqr_strerror(rc), q))
+    timed_launches = launches
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    total_flops = workload_flops() * args.steps * world
+    value = total_flops / elapsed / 1e9
+
+    per_q = {}
+    for q, e0, e1 in kt:
+        per_q.setdefault(q, []).append(e0.elapsed_time(e1) / 1e3)
+    kernel_time = sum(sum(v) for v in per_q.values()) / args.steps
+    achieved = workload_flops() / kernel_time / 1e12
+    detail = {str(q): {"gflops": flops(M, NB * q) / statistics.median(v) / 1e9,
+                       "ms": 1e3 * statistics.median(v),
+                       "critical_path_units": handles[q].info()["critical_path"]} for q, v in per_q.items()}
+
+    # End to end through the public API with host buffers (pinned).
+    e2e = None
+    if not args.no_e2e:
+        hosts, e2e_handles = {}, {}
+        for q in QS:
+            h = torch.empty((NB * q, M), dtype=torch.float64).pin_memory()
+            hosts[q] = h
+        h2d = sum(8 * M * NB * q for q in QS)
+
+        def e2e_step():
+            for q in QS:
+                a = hosts[q].numpy().T                      # Fortran view of pinned memory
+                e2e_handles[q] = tqr.tqr_factor_host(a, NB, IB, tqr.GREEDY, 1, stream=stream,
+                                                     reuse=e2e_handles.get(q))
+
+        # The host inputs are refilled from a host copy before each step (outside the timing).
+        host_src = {q: pristine[q].t().cpu().numpy() for q in QS}
+
+        def refill():
+            for q in QS:
+                hosts[q].numpy()[:] = host_src[q]
+
+        refill()
+        e2e_step()
+        torch.cuda.synchronize()
+        tsum = 0.0
+        for _ in range(args.e2e_steps):
+            refill()
+            if dist:
+                dist.barrier()
+            t_s = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            tsum += time.perf_counter() - t_s
+        if dist:
+            t = torch.tensor([tsum], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tsum = float(t.item())
+        e2e = {"value": workload_flops() * args.e2e_steps * world / tsum / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": args.e2e_steps,
+               "api": "tqr_factor_host (pinned host A in, R and V out)"}
+        for h in e2e_handles.values():
+            h.free()
+
+    if rank == 0:
+        line = {
+            "metric": "tiled-QR GFLOP/s (FP64)", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                         "kernel": "exec_kernel<4> (persistent executor; events around each tqr_factor)",
+                         "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": timed_launches,
+            "fp64_pct_of_peak": 100.0 * value / 1e3 / FP64_PEAK_TFLOPS / world,
+            "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    for h in handles.values():
+        h.free()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per executor launch from an ncu capture (for the roofline line)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_main(args)
+    return gpu_main(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
