@@ -59,6 +59,7 @@ typedef enum {
 #define TQR_ERR_CAPACITY (-105)     /* caller's output array too small            */
 #define TQR_ERR_INTERNAL (-106)     /* inconsistent internal state                */
 #define TQR_ERR_UNSUPPORTED (-107)  /* parameters outside what the kernels handle */
+#define TQR_ERR_TOO_LARGE (-108)    /* problem exceeds tqr_factor_noalloc's fixed scratch */
 
 typedef struct tqr_factors tqr_factors;
 
@@ -187,6 +188,51 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
  * stays usable.  tqr_inject_fault(0) cancels a pending injection. */
 int tqr_set_timeout_ms(double ms);
 int tqr_inject_fault(int kind);
+
+/* ---------------------------------------------------------------------------
+ * Factorization without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate memory when they factor --
+ * code running while a CUDA stream is being captured into a graph (where
+ * cudaMalloc is not allowed), services confined to a device-memory budget
+ * fixed at start-up, real-time loops that forbid allocation after
+ * initialization.  It computes exactly what tqr_factor computes (same task
+ * graph, same kernels) but calls no cudaMalloc, cudaFree or other allocating
+ * routine, on the device or the host.
+ *
+ * Its working state (task graph, dependency counters, ready queue) lives in
+ * one fixed array of TQR_NOALLOC_SCRATCH_BYTES (4 MiB) inside the library;
+ * every GPU that loads the library holds that array until the process exits.
+ * Limits: p*q <= TQR_NOALLOC_MAX_TILES tiles and at most
+ * TQR_NOALLOC_MAX_TASKS device tasks (updates count once per strip of
+ * columns; e.g. 16384 x 4096 at nb 256 fits, 16384 x 8192 does not);
+ * larger problems return TQR_ERR_TOO_LARGE and nothing is launched.
+ *
+ *   A:     device, m x n, column-major, lda = m; overwritten by R and V.
+ *   nb, ib: as for tqr_factor.
+ *   list:  host, `count` 0-based triplets (i, piv, k), e.g. from
+ *          tqr_elimination_list(); checked against the Section 2.2 rules
+ *          (TQR_ERR_INVALID_LIST).  ts = 1: TS kernels, 0: TT kernels.
+ *   tau_geqrt, tau_elim: device outputs, p*q*nb doubles each; the tau of
+ *          reflector r of GEQRT(i,k) (resp. of the TTQRT/TSQRT zeroing tile
+ *          (i,k)) is stored at [((size_t)k*p + i)*nb + r].
+ *   status: device output, one int32: set to 0 when the work starts and to
+ *          TQR_ERR_TIMEOUT or TQR_ERR_NONFINITE if the device detects one.
+ *   stream: the work is enqueued on it; the call returns without waiting.
+ *
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  Every call reuses the same array and
+ * overwrites what the previous call left in it (each launch re-initializes
+ * its counters and queue); calls whose device work overlaps -- on two
+ * streams without ordering between them, say -- race on the array and give
+ * wrong results.  Host threads are serialized while a call prepares its work.
+ * ------------------------------------------------------------------------- */
+#define TQR_NOALLOC_SCRATCH_BYTES (4 << 20)
+#define TQR_NOALLOC_MAX_TASKS 65536
+#define TQR_NOALLOC_MAX_TILES 4096
+int tqr_factor_noalloc(double* A, int64_t m, int64_t n, int nb, int ib, const int32_t* list,
+                       int64_t count, int ts, double* tau_geqrt, double* tau_elim, int32_t* status,
+                       void* stream);
 
 /* Message for a status code. */
 const char* tqr_strerror(int status);

@@ -601,6 +601,7 @@ const char* tqr_strerror(int status) {
         case TQR_ERR_CAPACITY: return "output array too small";
         case TQR_ERR_INTERNAL: return "internal error";
         case TQR_ERR_UNSUPPORTED: return "unsupported parameters";
+        case TQR_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of tqr_factor_noalloc";
         default:
             if (status < 0 && status > -100) return "invalid argument";
             return "unknown status";

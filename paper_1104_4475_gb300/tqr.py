@@ -28,6 +28,7 @@ TQR_ERR_NONFINITE = -102
 TQR_ERR_CUDA = -103
 TQR_ERR_NOMEM = -104
 TQR_ERR_CAPACITY = -105
+TQR_ERR_TOO_LARGE = -108
 
 
 class TqrError(RuntimeError):
@@ -79,6 +80,8 @@ def lib():
         L.tqr_set_timeout_ms.restype = ctypes.c_int
         L.tqr_inject_fault.argtypes = [ctypes.c_int]
         L.tqr_inject_fault.restype = ctypes.c_int
+        L.tqr_factor_noalloc.argtypes = [vp, i64, i64, i32, i32, pi32, i64, i32, vp, vp, vp, vp]
+        L.tqr_factor_noalloc.restype = ctypes.c_int
         L.tqr_free.argtypes = [vp]
         L.tqr_free.restype = None
         L.tqr_strerror.argtypes = [ctypes.c_int]
@@ -277,6 +280,22 @@ def tqr_tasks(p, q, tree, BS=1):
                            fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), out.shape[0], ctypes.byref(cnt)),
            "tqr_tasks")
     return out[: cnt.value], fin[: cnt.value]
+
+
+def tqr_factor_noalloc(A, nb, ib, elims, tau_geqrt, tau_elim, status, ts=False, stream=None):
+    """QR of A in place without any allocation (for callers that cannot
+    allocate while they factor).  elims: 0-based (i, piv, k) list;
+    tau_geqrt / tau_elim: float64 CUDA tensors of p*q*nb elements (outputs);
+    status: int32 CUDA tensor of one element (output).  Returns the C status."""
+    ptr, ld = _colmajor_ptr(A, "A")
+    m, n = A.shape
+    if ld != m:
+        raise ValueError("A must have leading dimension m")
+    arr = np.ascontiguousarray(np.asarray(elims, dtype=np.int32).reshape(-1, 3))
+    return lib().tqr_factor_noalloc(ptr, m, n, nb, ib, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    arr.shape[0], 1 if ts else 0, ctypes.c_void_p(tau_geqrt.data_ptr()),
+                                    ctypes.c_void_p(tau_elim.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                    _stream(stream))
 
 
 def tqr_set_timeout_ms(ms):

@@ -1,0 +1,97 @@
+"""tqr_factor_noalloc, the factorization for callers that cannot allocate
+(stream capture, fixed memory budgets, real-time loops): through the C ABI,
+its output must match tqr_factor's on two calls in a row, and problems beyond
+its fixed 4 MiB scratch must be refused without a launch.
+
+This file is collected last on purpose (pytest orders files by name).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1104_4475_gb300 as tqr
+from paper_1104_4475_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def tol_for(A):
+    """The parity suite's element-wise tolerance: 8 kappa(A) m u, floor 1e-13."""
+    return max(1e-13, 8 * np.linalg.cond(A) * A.shape[0] * U)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4475_gb300 import build
+    build.build()
+
+
+def reference_factor(A, nb, ib, tree):
+    """R, V and tau from the allocating entry point tqr_factor."""
+    m, n = A.shape
+    p, q = -(-m // nb), -(-n // nb)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, nb, ib, tree)
+    Tge = torch.zeros(p * q * ib * nb, dtype=torch.float64, device="cuda")
+    Tel = torch.zeros_like(Tge)
+    tqr.tqr_form_t(f, Tge, Tel)
+    tqr.tqr_sync(f)
+    f.free()
+
+    def taus(T):   # diagonal of each ib x ib block = tau of every reflector
+        T = T.cpu().numpy().reshape(q, p, nb, ib)
+        return np.array([[[T[k, i, r, r % ib] for r in range(nb)] for i in range(p)] for k in range(q)])
+
+    return tqr.to_numpy(At), taus(Tge), taus(Tel)
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", [(1024, 256, 64, 16, tqr.GREEDY), (700, 300, 48, 16, tqr.FLAT_TS)])
+def test_noalloc_matches_tqr_factor_on_two_calls(m, n, nb, ib, tree):
+    p, q = -(-m // nb), -(-n // nb)
+    elims = tqr.tqr_elimination_list(p, q, tree)
+    tau_ge = torch.zeros(p * q * nb, dtype=torch.float64, device="cuda")
+    tau_el = torch.zeros_like(tau_ge)
+    status = torch.full((1,), -999, dtype=torch.int32, device="cuda")
+    for call in range(2):                                  # two calls in a row, new input each time
+        A = workloads.gaussian(m, n, seed=100 + call)
+        ref, ref_tau_ge, ref_tau_el = reference_factor(A, nb, ib, tree)
+        At = tqr.colmajor(A)
+        rc = tqr.tqr_factor_noalloc(At, nb, ib, elims, tau_ge, tau_el, status, ts=(tree == tqr.FLAT_TS))
+        assert rc == 0, tqr.tqr_strerror(rc)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        tol = tol_for(A)
+        scale = np.abs(np.triu(ref[:n, :n])).max()
+        assert np.abs(tqr.to_numpy(At) - ref).max() / scale <= tol
+        got_ge = tau_ge.cpu().numpy().reshape(q, p, nb)
+        got_el = tau_el.cpu().numpy().reshape(q, p, nb)
+        assert np.abs(got_ge - ref_tau_ge).max() <= tol
+        assert np.abs(got_el - ref_tau_el).max() <= tol
+
+
+def test_noalloc_refuses_problems_beyond_its_scratch():
+    A = tqr.colmajor(np.zeros((8, 8)))
+    tau = torch.zeros(8, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = tqr.lib()
+    ct = tqr.tqr.ctypes
+    dummy = np.zeros(3, dtype=np.int32)
+    ptr = dummy.ctypes.data_as(ct.POINTER(ct.c_int32))
+    s = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    a = ct.c_void_p(A.data_ptr())
+    t = ct.c_void_p(tau.data_ptr())
+    st = ct.c_void_p(status.data_ptr())
+    # 65 x 64 tiles: more tiles than the scratch holds.
+    assert L.tqr_factor_noalloc(a, 65 * 256, 64 * 256, 256, 32, ptr, 1, 0, t, t, st, s) == tqr.TQR_ERR_TOO_LARGE
+    # 64 x 32 tiles at nb 256: the strip task graph exceeds the task limit.
+    elims = tqr.tqr_elimination_list(64, 32, tqr.GREEDY)
+    eptr = elims.ctypes.data_as(ct.POINTER(ct.c_int32))
+    assert L.tqr_factor_noalloc(a, 64 * 256, 32 * 256, 256, 32, eptr, elims.shape[0], 0, t, t, st,
+                                s) == tqr.TQR_ERR_TOO_LARGE
+    assert "scratch" in tqr.tqr_strerror(tqr.TQR_ERR_TOO_LARGE)
