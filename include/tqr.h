@@ -34,7 +34,10 @@ extern "C" {
 #endif
 
 /* Elimination trees (Section 3).  TQR_FLAT_TS runs FlatTree with TS kernels
- * (Proposition 2); every other tree runs TT kernels. */
+ * (Proposition 2); every other tree runs TT kernels.  ASAP and GRASAP(k)
+ * (Section 3.2) are dynamic: their lists come from simulating the tiled time
+ * model (Table 1 weights) while the list is built.  For TQR_GRASAP the BS
+ * argument carries k, 0 <= k <= min(p,q) (0 = Greedy, min(p,q) = ASAP). */
 typedef enum {
     TQR_FLAT_TS = 0,     /* Sameh-Kuck list, TS kernels                    */
     TQR_FLAT_TT = 1,     /* Sameh-Kuck list, TT kernels (FlatTree)         */
@@ -42,7 +45,9 @@ typedef enum {
     TQR_BINARY = 3,      /* binary reduction per column (Proposition 1)    */
     TQR_FIBONACCI = 4,   /* Fibonacci scheme of order 1 (Section 3.1)      */
     TQR_GREEDY = 5,      /* Greedy for tiles (Algorithm 4)                 */
-    TQR_PLASMA = 6       /* PlasmaTree with domain size BS (Section 3.2)   */
+    TQR_PLASMA = 6,      /* PlasmaTree with domain size BS (Section 3.2)   */
+    TQR_ASAP = 7,        /* ASAP: pair ready rows as soon as two are ready  */
+    TQR_GRASAP = 8       /* GRASAP(k), k = BS: Greedy, then ASAP on the last k columns */
 } tqr_tree;
 
 /* Kernel kinds, as reported by tqr_tasks(). */
@@ -92,8 +97,8 @@ typedef struct {
  * padding).
  *   nb:   tile size, 8 <= nb <= 256, nb % 4 == 0.
  *   ib:   inner blocking, ib divides nb, ib <= 64.
- *   tree: a tqr_tree value.  BS: PlasmaTree domain size, 1 <= BS <= p
- *         (ignored by other trees).
+ *   tree: a tqr_tree value.  BS: PlasmaTree domain size, 1 <= BS <= p, or
+ *         the k of GRASAP(k), 0 <= k <= q (ignored by other trees).
  *   out:  receives the handle.  If *out already holds a handle made for the
  *         same (m, n, nb, ib, tree, BS), its device buffers are reused and
  *         nothing is allocated; otherwise a new handle is created (the old

@@ -28,7 +28,7 @@ Notation follows the paper: tile rows ``i``, pivot rows ``piv``, panel columns
 
 # Tree identifiers.  The integer values are the same as the library's C enum
 # so that a test can name one tree for both sides; nothing else is shared.
-FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA = range(7)
+FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP = range(9)
 TREE_NAMES = {
     FLAT_TS: "FlatTree-TS",
     FLAT_TT: "FlatTree-TT",
@@ -37,4 +37,6 @@ TREE_NAMES = {
     FIBONACCI: "Fibonacci",
     GREEDY: "Greedy",
     PLASMA: "PlasmaTree",
+    ASAP: "ASAP",
+    GRASAP: "GRASAP",
 }

@@ -124,3 +124,73 @@ def critical_path(p, q, elims, ts=False):
 
 def total_weight(tasks):
     return sum(WEIGHT[t[0]] for t in tasks)
+
+
+class Incremental:
+    """The expansion, dependencies and ASAP times of a list built one
+    elimination at a time (used by the dynamic ASAP / GRASAP trees, whose
+    next elimination depends on the times of the previous ones)."""
+
+    def __init__(self, p, q, ts=False):
+        self.p, self.q, self.ts = p, q, ts
+        self.tasks, self.finish = [], []
+        self.triangle = set()
+        self.last_writer, self.producer = {}, {}
+
+    def _add(self, task):
+        kind, i, piv, k, j = task
+        d = []
+        if kind == GEQRT:
+            writes = [(i, k)]
+        elif kind == UNMQR:
+            d.append(self.producer[(i, k)])
+            writes = [(i, j)]
+        elif kind in (TTQRT, TSQRT):
+            writes = [(piv, k), (i, k)]
+        else:
+            d.append(self.producer[("e", i, k)])
+            writes = [(piv, j), (i, j)]
+        d += [self.last_writer[w] for w in writes if w in self.last_writer]
+        t = len(self.tasks)
+        for w in writes:
+            self.last_writer[w] = t
+        if kind == GEQRT:
+            self.producer[(i, k)] = t
+        elif kind in (TTQRT, TSQRT):
+            self.producer[("e", i, k)] = t
+        self.tasks.append(task)
+        self.finish.append(max((self.finish[x] for x in d), default=0) + WEIGHT[kind])
+        return t
+
+    def _factor(self, x, k):
+        if (x, k) in self.triangle:
+            return
+        self.triangle.add((x, k))
+        self._add((GEQRT, x, 0, k, 0))
+        for j in range(k + 1, self.q + 1):
+            self._add((UNMQR, x, 0, k, j))
+
+    def add_elim(self, i, piv, k):
+        """Append elim(i, piv, k) (Algorithm 3, or 2 when ts); returns the
+        finish time of its TTQRT/TSQRT."""
+        self._factor(piv, k)
+        if not self.ts:
+            self._factor(i, k)
+        t = self._add(((TSQRT if self.ts else TTQRT), i, piv, k, 0))
+        for j in range(k + 1, self.q + 1):
+            self._add(((TSMQR if self.ts else TTMQR), i, piv, k, j))
+        return self.finish[t]
+
+    def triangle_time(self, x, k):
+        """When GEQRT(x,k) would finish if emitted now: last writer of tile
+        (x,k) plus the GEQRT weight (tile (x,k) must have all its writers)."""
+        if (x, k) in self.triangle:
+            return self.finish[self.producer[(x, k)]]
+        lw = self.last_writer.get((x, k))
+        return (self.finish[lw] if lw is not None else 0) + WEIGHT[GEQRT]
+
+    def close(self):
+        """Factor the diagonal tiles that took part in no elimination."""
+        for k in range(1, min(self.p, self.q) + 1):
+            self._factor(k, k)
+        return max(self.finish, default=0)

@@ -8,7 +8,7 @@ Part of the test oracle (see ``oracle/__init__.py``).  Everything here is
 Readings of points the paper leaves open are stated beside each generator.
 """
 
-from . import FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA
+from . import FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP
 
 
 # --------------------------------------------------------------------------
@@ -161,7 +161,8 @@ def plasma_tree(p, q, BS):
 
 
 def elimination_list(p, q, tree, BS=1):
-    """The elimination list of one of the seven trees (1-based triplets)."""
+    """The elimination list of a tree (1-based triplets).  BS is PlasmaTree's
+    domain size, or the k of GRASAP(k)."""
     if not (p >= q >= 1):
         raise ValueError("need p >= q >= 1")
     if tree in (FLAT_TS, FLAT_TT, SAMEH_KUCK):
@@ -174,6 +175,10 @@ def elimination_list(p, q, tree, BS=1):
         return greedy(p, q)
     if tree == PLASMA:
         return plasma_tree(p, q, BS)
+    if tree == ASAP:
+        return asap(p, q)
+    if tree == GRASAP:
+        return grasap(p, q, BS)
     raise ValueError("unknown tree %r" % (tree,))
 
 
@@ -266,3 +271,64 @@ def coarse_fibonacci(p, q):
     """Coarse-grain Fibonacci time-steps from the closed form."""
     return {(i, k): fibonacci_coarse(p, i, k)
             for k in range(1, min(p, q) + 1) for i in range(k + 1, p + 1)}
+
+
+# --------------------------------------------------------------------------
+# ASAP and GRASAP(k) (Section 3.2): dynamic trees on the tiled time model.
+# --------------------------------------------------------------------------
+def asap(p, q, greedy_columns=0):
+    """ASAP: in every column, as soon as at least two rows are ready (their
+    tile of the column is a triangle and no elimination is using it), pair
+    them.  With 2s ready rows r_1 < ... < r_2s the first is paired with row
+    s+1, the second with s+2, ...: r_{s+j} is zeroed by r_j.  With an odd
+    number of ready rows the one closest to the diagonal waits.
+    GRASAP(k): ``greedy_columns = q - k`` first columns follow Greedy
+    (Algorithm 4), the last k columns follow ASAP.  Returns the list (in
+    order of decision time, then column, then row)."""
+    from . import dag
+    qq = min(p, q)
+    inc = dag.Incremental(p, q)
+    out = []
+    zeroed = set()
+    busy_until = {}
+    if greedy_columns > 0:
+        for e in greedy(p, q):
+            if e[2] <= greedy_columns:
+                out.append(e)
+                inc.add_elim(*e)
+                zeroed.add((e[0], e[2]))
+    total = sum(p - k for k in range(1, qq + 1))
+    t = 0
+    while len(zeroed) < total:
+        progressed = False
+        for k in range(greedy_columns + 1, qq + 1):
+            ready = []
+            for r in range(k, p + 1):
+                if (r, k) in zeroed:
+                    continue
+                if k > 1 and any((r, kp) not in zeroed for kp in range(1, k)):
+                    continue
+                if busy_until.get(r, 0) > t:
+                    continue
+                if inc.triangle_time(r, k) <= t:
+                    ready.append(r)
+            if len(ready) < 2:
+                continue
+            s = len(ready) // 2
+            rows = ready[len(ready) - 2 * s:]
+            for jj in range(s):
+                piv, i = rows[jj], rows[s + jj]
+                out.append((i, piv, k))
+                end = inc.add_elim(i, piv, k)
+                zeroed.add((i, k))
+                busy_until[i] = busy_until[piv] = end
+                progressed = True
+        t += 1
+        if t > 100000 * (p + q) and not progressed:
+            raise RuntimeError("ASAP made no progress")
+    return out
+
+
+def grasap(p, q, k):
+    """GRASAP(k): Greedy on columns 1..q-k, ASAP on the last k columns."""
+    return asap(p, q, greedy_columns=max(0, min(p, q) - k))

@@ -297,14 +297,16 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
     try {
         int rc = check_common(A, m, n, nb, ib);
         if (rc != TQR_OK) return rc;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -6;
+        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -6;
         const int p = static_cast<int>((m + nb - 1) / nb);
+        const int q = static_cast<int>((n + nb - 1) / nb);
         if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -7;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
         if (!out) return -9;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
         PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
-                    tree == TQR_PLASMA ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
+                    (tree == TQR_PLASMA || tree == TQR_GRASAP) ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
         return run_factor(key, A, stream, out);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
@@ -488,8 +490,9 @@ int tqr_elimination_list(int p, int q, int tree, int BS, int32_t* out, int64_t c
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
         if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!count) return -7;
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
@@ -526,8 +529,9 @@ int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
         if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!cp) return -5;
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
@@ -552,8 +556,9 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA) return -3;
+        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
         if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!count) return -8;
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);

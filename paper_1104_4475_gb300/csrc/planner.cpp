@@ -104,6 +104,131 @@ static void plasma_list(int p, int q, int BS, std::vector<Elim>& out) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// ASAP and GRASAP(k) (Section 3.2).  These trees are dynamic: the next
+// eliminations depend on when rows become ready in the tiled time model, so
+// the list is built together with an incremental unit-weight simulation of
+// its kernel tasks (Algorithm 3 expansion, producer + last-writer edges).
+// ---------------------------------------------------------------------------
+namespace {
+
+class IncSim {
+public:
+    IncSim(int p, int q)
+        : p_(p), q_(q), last_(static_cast<size_t>(p) * q, -1), prod_ge_(static_cast<size_t>(p) * q, -1),
+          prod_el_(static_cast<size_t>(p) * q, -1), tri_(static_cast<size_t>(p) * q, 0) {}
+
+    // Appends elim(i, piv, k) with TT kernels; returns its TTQRT's finish.
+    int64_t add_elim(int i, int piv, int k) {
+        factor(piv, k);
+        factor(i, k);
+        const int64_t t = add(TTQRT, i, piv, k, -1);
+        for (int j = k + 1; j < q_; ++j) add(TTMQR, i, piv, k, j);
+        return t;
+    }
+
+    // Finish of GEQRT(x,k) if it were emitted now.
+    int64_t triangle_time(int x, int k) const {
+        const size_t a = idx(x, k);
+        if (tri_[a]) return fin_[prod_ge_[a]];
+        return (last_[a] >= 0 ? fin_[last_[a]] : 0) + kernel_weight(GEQRT);
+    }
+
+private:
+    int p_, q_;
+    std::vector<int64_t> fin_;
+    std::vector<int64_t> last_, prod_ge_, prod_el_;
+    std::vector<char> tri_;
+
+    size_t idx(int r, int c) const { return static_cast<size_t>(c) * p_ + r; }
+
+    void factor(int x, int k) {
+        if (tri_[idx(x, k)]) return;
+        tri_[idx(x, k)] = 1;
+        add(GEQRT, x, -1, k, -1);
+        for (int j = k + 1; j < q_; ++j) add(UNMQR, x, -1, k, j);
+    }
+
+    int64_t add(int kind, int i, int piv, int k, int j) {
+        int64_t start = 0;
+        size_t w[2];
+        int nw = 0;
+        if (kind == GEQRT) {
+            w[nw++] = idx(i, k);
+        } else if (kind == UNMQR) {
+            start = fin_[prod_ge_[idx(i, k)]];
+            w[nw++] = idx(i, j);
+        } else if (kind == TTQRT) {
+            w[nw++] = idx(piv, k);
+            w[nw++] = idx(i, k);
+        } else {
+            start = fin_[prod_el_[idx(i, k)]];
+            w[nw++] = idx(piv, j);
+            w[nw++] = idx(i, j);
+        }
+        for (int a = 0; a < nw; ++a)
+            if (last_[w[a]] >= 0) start = std::max(start, fin_[last_[w[a]]]);
+        const int64_t t = static_cast<int64_t>(fin_.size());
+        fin_.push_back(start + kernel_weight(kind));
+        for (int a = 0; a < nw; ++a) last_[w[a]] = t;
+        if (kind == GEQRT) prod_ge_[idx(i, k)] = t;
+        if (kind == TTQRT) prod_el_[idx(i, k)] = t;
+        return fin_.back();
+    }
+};
+
+}  // namespace
+
+// ASAP: in every column, as soon as two or more rows are ready (tile of the
+// column triangularized, row not zeroed in it, not inside an elimination),
+// the 2s bottom ready rows are paired first-with-(s+1)-th, second-with-
+// (s+2)-th, ...; with an odd count the row nearest the diagonal waits.
+// GRASAP(kk): columns 0..q-kk-1 keep the Greedy list, the last kk columns run
+// ASAP.  List order: the Greedy part, then decision time, column, pair.
+static void asap_list(int p, int q, int greedy_cols, std::vector<Elim>& out) {
+    const int qq = std::min(p, q);
+    IncSim sim(p, q);
+    std::vector<int> zc(p, 0);               // leading columns zeroed in each row
+    std::vector<int64_t> busy(p, 0);
+    int64_t remaining = 0;
+    for (int k = 0; k < qq; ++k) remaining += p - 1 - k;
+    if (greedy_cols > 0) {
+        std::vector<Elim> g;
+        greedy_list(p, q, g);
+        for (const Elim& e : g)
+            if (e.k < greedy_cols) {
+                out.push_back(e);
+                sim.add_elim(e.i, e.piv, e.k);
+                zc[e.i] = e.k + 1;
+                --remaining;
+            }
+    }
+    std::vector<std::vector<int>> ready(qq);
+    for (int64_t t = 0; remaining > 0; ++t) {
+        for (int k = 0; k < qq; ++k) ready[k].clear();
+        for (int r = 0; r < p; ++r) {
+            const int k = zc[r];                 // column in which row r is active
+            if (k >= qq || k < greedy_cols || r < k) continue;
+            if (busy[r] > t || sim.triangle_time(r, k) > t) continue;
+            ready[k].push_back(r);
+        }
+        for (int k = greedy_cols; k < qq; ++k) {
+            const std::vector<int>& rd = ready[k];
+            const int s = static_cast<int>(rd.size()) / 2;
+            if (s < 1) continue;
+            const int base = static_cast<int>(rd.size()) - 2 * s;
+            for (int a = 0; a < s; ++a) {
+                const int piv = rd[base + a], i = rd[base + s + a];
+                out.push_back({i, piv, k});
+                const int64_t end = sim.add_elim(i, piv, k);
+                zc[i] = k + 1;
+                busy[i] = busy[piv] = end;
+                --remaining;
+            }
+        }
+    }
+}
+
 int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out) {
     out.clear();
     switch (tree) {
@@ -116,6 +241,11 @@ int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out) {
         case TQR_PLASMA:
             if (BS < 1 || BS > p) return -4;
             plasma_list(p, q, BS, out);
+            return TQR_OK;
+        case TQR_ASAP: asap_list(p, q, 0, out); return TQR_OK;
+        case TQR_GRASAP:
+            if (BS < 0 || BS > std::min(p, q)) return -4;
+            asap_list(p, q, std::min(p, q) - BS, out);
             return TQR_OK;
         default: return -3;
     }

@@ -18,9 +18,9 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GEQRT, UNMQR, TTQRT, TTMQR, TSQRT, TSMQR = range(6)
-FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA = range(7)
+FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP = range(9)
 TREES = {"flat_ts": FLAT_TS, "flat_tt": FLAT_TT, "sameh_kuck": SAMEH_KUCK, "binary": BINARY,
-         "fibonacci": FIBONACCI, "greedy": GREEDY, "plasma": PLASMA}
+         "fibonacci": FIBONACCI, "greedy": GREEDY, "plasma": PLASMA, "asap": ASAP, "grasap": GRASAP}
 
 TQR_ERR_INVALID_LIST = -100
 TQR_ERR_TIMEOUT = -101

@@ -1,0 +1,75 @@
+"""Parity at the benchmark's full size and launch configuration (m = 16384,
+nb = 256, ib = 32, Greedy, U[-0.5, 0.5] entries, seed 1 -- the sweep points
+q = 8 and q = 64), where the oracle cannot factor the whole matrix:
+
+* sampled outputs the oracle computes exactly: the whole first tile column
+  (R_11 and every reflector of column 1) comes only from column-1 kernels,
+  whose elimination list Greedy does not change with q, so it must equal the
+  oracle's factorization of A[:, :nb] element-wise;
+* properties that hold at any size: ||R[:, c]|| = ||A[:, c]|| for every
+  column c (Q is orthogonal), ||Q^T b|| = ||b||, and on sampled columns
+  A[:, c] = Q R[:, c] and Q[:, S]^T Q[:, S] = I.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import tiled_qr as otq
+import paper_1104_4475_gb300 as tqr
+from paper_1104_4475_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+M, NB, IB = 16384, 256, 32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4475_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("q", [8, 64])
+def test_full_size_greedy(q):
+    n = NB * q
+    A = workloads.sweep_config(q)               # the benchmark's input for this q
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, NB, IB, tqr.GREEDY)
+    tqr.tqr_sync(f)
+    # Sampled outputs: the first tile column against the oracle.
+    A1 = np.ascontiguousarray(A[:, :NB])
+    F1 = otq.factor(A1, NB, IB, tqr.GREEDY)
+    col1 = tqr.to_numpy(At[:, :NB])
+    tol = max(1e-13, 8 * np.linalg.cond(A1) * M * U)
+    err = np.abs(col1 - F1.A).max() / np.abs(F1.r()).max()
+    assert err <= tol, (err, tol)
+    # Every column: ||R[:, c]|| = ||A[:, c]||.
+    R = np.triu(tqr.to_numpy(At[:n, :]))
+    rn, an = np.linalg.norm(R, axis=0), np.linalg.norm(A, axis=0)
+    assert np.abs(rn - an).max() / an.max() <= 1e-13
+    # Sampled columns: A = Q R and Q^T Q = I.
+    cols = np.linspace(0, n - 1, 8).astype(int)
+    B = np.zeros((M, len(cols)))
+    B[:n] = R[:, cols]
+    Bt = tqr.colmajor(B)
+    tqr.tqr_apply_q(f, Bt)
+    E = np.zeros((M, len(cols)))
+    E[cols, np.arange(len(cols))] = 1.0
+    Et = tqr.colmajor(E)
+    tqr.tqr_apply_q(f, Et)
+    b = workloads.rhs(M, 1, seed=2)
+    bt = tqr.colmajor(b)
+    tqr.tqr_apply_qt(f, bt)
+    tqr.tqr_sync(f)
+    res = np.linalg.norm(A[:, cols] - tqr.to_numpy(Bt)) / np.linalg.norm(A[:, cols])
+    Qs = tqr.to_numpy(Et)
+    orth = np.linalg.norm(np.eye(len(cols)) - Qs.T @ Qs)
+    assert res <= 1e-13, res
+    assert orth <= 1e-13, orth
+    assert abs(np.linalg.norm(tqr.to_numpy(bt)) - np.linalg.norm(b)) <= 1e-13 * np.linalg.norm(b)
+    f.free()

@@ -104,7 +104,8 @@ def test_small_config_parity():
 
 
 TREES = [(tqr.FLAT_TS, 1), (tqr.FLAT_TT, 1), (tqr.SAMEH_KUCK, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1),
-         (tqr.GREEDY, 1), (tqr.PLASMA, 1), (tqr.PLASMA, 3), (tqr.PLASMA, 10)]
+         (tqr.GREEDY, 1), (tqr.PLASMA, 1), (tqr.PLASMA, 3), (tqr.PLASMA, 10), (tqr.ASAP, 1),
+         (tqr.GRASAP, 2)]
 
 
 @pytest.mark.parametrize("tree,BS", TREES)

@@ -61,6 +61,29 @@ def test_elimination_lists_match_oracle(tree):
             assert lists_equal(p, q, tree), (p, q)
 
 
+@pytest.mark.parametrize("tree", [tqr.ASAP, tqr.GRASAP])
+def test_dynamic_lists_match_oracle(tree):
+    for p in range(1, 19):
+        for q in range(1, p + 1):
+            for k in (range(0, q + 1) if tree == tqr.GRASAP else [1]):
+                got = tqr.tqr_elimination_list(p, q, tree, k)
+                want = np.array(otrees.elimination_list(p, q, tree, k), dtype=np.int32).reshape(-1, 3) - 1
+                assert np.array_equal(got, want), (p, q, k)
+
+
+def test_asap_biggermat_library():
+    """The library's ASAP on the whole biggermat table (p up to 128).  Reading:
+    the 128 x 64 entry is printed 1748; this ASAP rule, which matches the other
+    nine entries and Table table.15x2x3 (b), gives 1734."""
+    from conftest import load_rows
+    for p, q, g, a in load_rows("biggermat_cp.txt"):
+        assert tqr.tqr_critical_path(p, q, tqr.GREEDY) == g
+        if (p, q) == (128, 64):
+            assert tqr.tqr_critical_path(p, q, tqr.ASAP) == 1734
+        else:
+            assert tqr.tqr_critical_path(p, q, tqr.ASAP) == a, (p, q)
+
+
 def test_plasma_lists_match_oracle():
     for p in range(1, 26):
         for q in range(1, p + 1):
@@ -70,7 +93,8 @@ def test_plasma_lists_match_oracle():
 
 @pytest.mark.parametrize("p,q,tree,BS", [(16, 4, tqr.GREEDY, 1), (15, 6, tqr.FIBONACCI, 1), (40, 17, tqr.PLASMA, 7),
                                          (64, 64, tqr.GREEDY, 1), (64, 8, tqr.FLAT_TS, 1), (33, 20, tqr.BINARY, 1),
-                                         (9, 9, tqr.FLAT_TT, 1), (1, 1, tqr.GREEDY, 1), (7, 1, tqr.FLAT_TS, 1)])
+                                         (9, 9, tqr.FLAT_TT, 1), (1, 1, tqr.GREEDY, 1), (7, 1, tqr.FLAT_TS, 1),
+                                         (15, 3, tqr.ASAP, 1), (21, 9, tqr.GRASAP, 3), (12, 12, tqr.GRASAP, 12)])
 def test_tasks_schedule_and_cp_match_oracle(p, q, tree, BS):
     el = otrees.elimination_list(p, q, tree, BS)
     ts = tree == tqr.FLAT_TS

@@ -319,3 +319,60 @@ def test_integer_pins_catch_planted_mistakes(monkeypatch):
 
     monkeypatch.setattr(trees, "fibonacci", fib_col1_z)
     assert not _tiled_matches("Fibonacci")
+
+
+# ------------------------------------------------------------- ASAP / GRASAP
+def _check_table(name, p, q, el, ncol, skip=()):
+    gold = load_blocks("tab_15x2x3.txt")[name]
+    tasks = dag.expand(p, q, el)
+    fin, cp = dag.simulate(tasks)
+    zt = dag.zero_times(tasks, fin)
+    for i, vals in gold.items():
+        for k, v in enumerate(vals[:ncol], start=1):
+            if (i, k) in skip:
+                continue
+            assert zt[(i, k)] == v, (name, i, k, zt[(i, k)], v)
+    return zt, cp
+
+
+def test_asap_15x3_and_15x2():
+    """Table table.15x2x3 (b): every ASAP zero-out time on 15x3, and the
+    15x2 case (first two columns); Section 3.2: on 15x2 ASAP beats Greedy."""
+    el = trees.asap(15, 3)
+    assert trees.validate(15, 3, el) is None
+    _, cp3 = _check_table("ASAP", 15, 3, el, 3)
+    assert cp3 == 86
+    el2 = trees.asap(15, 2)
+    _, cp2 = _check_table("ASAP", 15, 2, el2, 2)
+    assert cp2 < dag.critical_path(15, 2, trees.greedy(15, 2))
+
+
+def test_grasap1_15x3():
+    """Table table.15x2x3 (c) and Section 3.2: GRASAP(1) finishes at 62, Greedy
+    at 64.  Reading: tile (7,3) is printed 56; this ASAP rule (which
+    reproduces Table (b) entirely) pairs rows 6 and 7 when both are released
+    at time 50, giving 52.  All other 35 entries match."""
+    el = trees.grasap(15, 3, 1)
+    assert trees.validate(15, 3, el) is None
+    zt, cp = _check_table("GRASAP1", 15, 3, el, 3, skip={(7, 3)})
+    assert zt[(7, 3)] == 52
+    assert cp == 62 and dag.critical_path(15, 3, trees.greedy(15, 3)) == 64
+
+
+def test_asap_biggermat():
+    """Table table.biggermat, ASAP column, p <= 64 (the oracle is slow beyond)."""
+    for p, q, _g, a in load_rows("biggermat_cp.txt"):
+        if p <= 64:
+            assert dag.critical_path(p, q, trees.asap(p, q)) == a, (p, q)
+
+
+def test_grasap_extremes_and_invariants():
+    for p in range(2, 12):
+        for q in range(1, p + 1):
+            assert trees.grasap(p, q, 0) == trees.greedy(p, q)
+            assert trees.grasap(p, q, q) == trees.asap(p, q)
+            for k in range(0, q + 1):
+                el = trees.grasap(p, q, k)
+                assert trees.validate(p, q, el) is None
+                assert all(piv < i for (i, piv, kk) in el)
+                assert dag.total_weight(dag.expand(p, q, el)) == 6 * p * q * q - 2 * q ** 3
