@@ -330,12 +330,78 @@ def gpu_main(args):
     return 0
 
 
+# ----------------------------------------------------- mixed-precision LS
+LS_M, LS_N, LS_NB, LS_IB = 65536, 4096, 256, 32
+LS_KAPPAS = (1e2, 1e6, 1e10)
+
+
+def lstsq_main(args):
+    """Mixed-precision least squares (split-TF32 updates, FP64 panels, FP64
+    refinement) against the FP64 path on A = U diag(sigma) V^T, 65536 x 4096,
+    kappa in {1e2, 1e6, 1e10}, b = A x_true + 1e-10 N(0,1).  Times are wall
+    clock around tqr_lstsq (A, b, x resident on the device), best of
+    ``--steps`` after one warm-up call."""
+    import torch
+    import paper_1104_4475_gb300 as tqr
+    from paper_1104_4475_gb300 import build, workloads
+    build.build()
+    torch.cuda.set_device(0)
+    detail = {}
+    for kappa in LS_KAPPAS:
+        A, b, x_true = workloads.ls_problem_device(LS_M, LS_N, kappa, seed=3)
+        torch.cuda.synchronize()
+
+        def run(prec, tol, maxit):
+            best, info, x = None, None, None
+            for rep in range(1 + max(1, args.steps)):
+                x = torch.zeros(LS_N, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = tqr.tqr_lstsq(A, b, x, LS_NB, LS_IB, tqr.GREEDY, 1, prec, tol, maxit)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if rep > 0:
+                    best = dt if best is None else min(best, dt)
+            return best, info, x
+
+        t64, i64, x64 = run(tqr.TQR_FP64, 0.0, 0)
+        eta64 = i64["backward_error"]
+        tmx, imx, xmx = run(tqr.TQR_SPLIT_TF32, eta64, 200)
+        nx = float(torch.linalg.norm(x_true))
+        rec = {
+            "fp64_seconds": t64, "mixed_seconds": tmx,
+            "speedup": (t64 / tmx) if imx["converged"] else None,
+            "fp64_backward_error": eta64, "mixed_backward_error": imx["backward_error"],
+            "converged": bool(imx["converged"]),
+            "refine_iterations": imx["refine_iterations"], "cgls_iterations": imx["cgls_iterations"],
+            "fp64_factor_seconds": i64["factor_seconds"], "mixed_factor_seconds": imx["factor_seconds"],
+            "forward_error_fp64_vs_true": float(torch.linalg.norm(x64 - x_true)) / nx,
+            "forward_error_mixed_vs_true": float(torch.linalg.norm(xmx - x_true)) / nx,
+            "forward_error_mixed_vs_fp64": float(torch.linalg.norm(xmx - x64)) / float(torch.linalg.norm(x64)),
+        }
+        detail["%g" % kappa] = rec
+        del A, b, x_true
+        torch.cuda.empty_cache()
+    head = detail["%g" % 1e6]
+    line = {"metric": "mixed-prec LS speedup at FP64 backward error", "value": head["speedup"], "unit": "x",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+tf32x3", "data": "synthetic",
+            "config": {"workload": "least squares A = U diag(sigma) V^T, m=65536, n=4096, sigma log-spaced "
+                                   "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
+                       "nb": LS_NB, "ib": LS_IB, "tree": "Greedy", "kappas": list(LS_KAPPAS)},
+            "detail": detail}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "lstsq"],
+                    help="sweep: FP64 tree sweep (default); lstsq: mixed-precision least squares")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -346,6 +412,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_main(args)
+    if args.workload == "lstsq":
+        return lstsq_main(args)
     return gpu_main(args)
 
 

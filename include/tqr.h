@@ -68,6 +68,27 @@ typedef enum {
 
 typedef struct tqr_factors tqr_factors;
 
+/* Arithmetic of the update kernels (UNMQR/TSMQR/TTMQR).  Panels (reflector
+ * generation, T factors) and everything a least-squares solve does with A and
+ * its residual stay FP64 in every mode. */
+typedef enum {
+    TQR_FP64 = 0,        /* FP64 everywhere                                   */
+    TQR_SPLIT_TF32 = 1,  /* updates on tensor cores, operands split hi+lo TF32, 3 products, FP32 accumulation */
+    TQR_TF32 = 2         /* updates on tensor cores, one TF32 product, FP32 accumulation */
+} tqr_precision;
+
+/* Result of tqr_lstsq. */
+typedef struct {
+    int32_t refine_iterations;  /* FP64 refinement steps taken                       */
+    int32_t cgls_iterations;    /* R-preconditioned CGLS steps taken                  */
+    int32_t converged;          /* 1 if the backward error reached tol (always 1 in FP64) */
+    int32_t status;             /* device status of the factorization                */
+    double backward_error;      /* ||A^T r||_2 / (||A||_F ||r||_2), r = b - A x      */
+    double residual_norm;       /* ||r||_2                                           */
+    double factor_seconds;      /* factorization + Q^T b, wall time                  */
+    double solve_seconds;       /* inverse of R, solution and refinement, wall time  */
+} tqr_lstsq_info;
+
 /* Summary of a factorization handle. */
 typedef struct {
     int64_t m, n;          /* matrix size                                  */
@@ -108,6 +129,16 @@ typedef struct {
 int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
                void* stream, tqr_factors** out);
 
+/* tqr_factor with a choice of update arithmetic (tqr_precision).  With
+ * TQR_SPLIT_TF32 / TQR_TF32 the panel kernels also form the compact-WY T of
+ * each block of ib reflectors in FP64, and the update kernels apply
+ * C <- C - V (T^T (V^T C)) with both products on the tensor cores; A (R and V)
+ * stays FP64.  Low precision needs nb % 16 == 0 and ib in {16, 32, 64, 128}
+ * (else TQR_ERR_UNSUPPORTED).  Argument errors: as tqr_factor, -8 for an
+ * unknown precision, -10 for out. */
+int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, int precision,
+                  void* stream, tqr_factors** out);
+
 /* Same with a caller-given elimination list: `list` (host) holds `count`
  * 0-based triplets (i, piv, k) in order; ts = 1 selects TS kernels, 0 TT.
  * The list is checked against the rules of Section 2.2 first
@@ -134,6 +165,18 @@ int tqr_apply_q(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, void* stre
  * such a kernel are set to zero.  Either pointer may be NULL. */
 int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream);
 
+/* Per-task trace of the last factorization on a handle (profiling; the
+ * paper's simulator has no device counterpart).  tqr_set_trace(f, 1) makes
+ * later factorizations with f record, for every device task, its start and
+ * end on the GPU's %globaltimer (ns) and the SM that ran it (allocates
+ * 16 bytes per task once).  tqr_get_trace waits for the handle's work and
+ * writes 8 int64 per task to out (host): kind, i, piv, k, j * 65536 + strip,
+ * start ns, end ns, SM id -- in device task order; cap in tasks, *count =
+ * number of tasks (TQR_ERR_CAPACITY if cap is too small,
+ * TQR_ERR_UNSUPPORTED if tracing was not enabled). */
+int tqr_set_trace(tqr_factors* f, int enable);
+int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count);
+
 /* Waits for the handle's last enqueued work and returns its device status:
  * TQR_OK, TQR_ERR_TIMEOUT, TQR_ERR_NONFINITE or TQR_ERR_CUDA. */
 int tqr_sync(tqr_factors* f);
@@ -152,6 +195,23 @@ void tqr_free(tqr_factors* f);
  * *out = NULL before the first call).  Synchronizes before returning. */
 int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
                     double* B_host, int64_t nrhs, void* stream, tqr_factors** out);
+
+/* Least squares min ||A x - b||_2 (Section 1 names least squares as the main
+ * use of the factorization).  A: device, m x n (m >= n), column-major, lda = m,
+ * left unchanged (the library factors a copy); b: device, m; x: device, n,
+ * output.  The copy of A is factored with `precision`; c = Q^T b is formed with
+ * the reflectors in FP64; x = R^-1 c[0:n] with an explicit FP64 inverse of R.
+ * For a low-precision factorization x is then refined in FP64 -- residual
+ * r = b - A x, correction R^-1 R^-T A^T r -- until the backward error
+ * ||A^T r|| / (||A||_F ||r||) <= tol; if a step fails to halve it, CGLS on the
+ * correction problem, right-preconditioned by R^-1, continues, for at most
+ * maxit steps in all.  info (host, may be NULL) receives iteration counts,
+ * final backward error and phase times.  Synchronizes `stream` before
+ * returning.  Allocates device workspace (m*n + n*n doubles + vectors) for the
+ * call. */
+int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b, double* x, int nb, int ib,
+              int tree, int BS, int precision, double tol, int maxit, void* stream,
+              tqr_lstsq_info* info);
 
 /* ---------------------------------------------------------------------------
  * Host-only integer entry points (no GPU needed).

@@ -201,6 +201,11 @@ struct tqr_factors {
     double* tau_el = nullptr;
     int32_t* status = nullptr;
     ExecState fst, ast;
+    double* T_ge = nullptr;      // compact-WY T blocks (low-precision factorizations)
+    double* T_el = nullptr;
+    int prec = 0;
+    uint64_t* trace = nullptr;   // per-task (start, duration | sm << 56) when tracing
+    int trace_on = 0;
     double* own_A = nullptr;     // device copies used by tqr_factor_host
     double* own_B = nullptr;
     size_t own_B_elems = 0;
@@ -209,6 +214,9 @@ struct tqr_factors {
         free_state(ast);
         cudaFree(tau_ge);
         cudaFree(tau_el);
+        cudaFree(T_ge);
+        cudaFree(T_el);
+        cudaFree(trace);
         cudaFree(status);
         cudaFree(own_A);
         cudaFree(own_B);
@@ -240,6 +248,10 @@ static ExecParams base_params(const tqr_factors* f) {
     x.tau_ge = f->tau_ge;
     x.tau_el = f->tau_el;
     x.trans = 1;
+    x.prec = f->prec;
+    x.T_ge = f->T_ge;
+    x.T_el = f->T_el;
+    x.trace = nullptr;
     x.timeout_ns = timeout_ns(lapack_flops(P.key.m, P.key.n));
     return x;
 }
@@ -261,20 +273,42 @@ static int new_handle(const std::shared_ptr<Plan>& plan, tqr_factors** out) {
     return TQR_OK;
 }
 
-static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors** out) {
+static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors** out, int prec = 0) {
     std::shared_ptr<Plan> plan;
     int rc = get_plan(key, plan);
     if (rc != TQR_OK) return rc;
+    int smem = plan->smem;
+    if (prec != 0) {
+        if (!lp_supported(key.nb, key.ib, plan->G)) return TQR_ERR_UNSUPPORTED;
+        smem = std::max(smem, lp_smem_bytes(key.nb, key.ib, plan->G));
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (smem > maxsm - 1024) return TQR_ERR_UNSUPPORTED;
+    }
     tqr_factors* f = *out;
     if (!f || f->plan != plan) {
         rc = new_handle(plan, &f);
         if (rc != TQR_OK) return rc;
     }
+    if (prec != 0 && !f->T_ge) {
+        const size_t nt = static_cast<size_t>(plan->p) * plan->q * key.ib * key.nb;
+        if (cudaMalloc(&f->T_ge, nt * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&f->T_el, nt * sizeof(double)) != cudaSuccess) {
+            if (f != *out) delete f;
+            return TQR_ERR_NOMEM;
+        }
+    }
     f->A = A;
+    f->prec = prec;
     f->stream = static_cast<cudaStream_t>(stream);
+    if (f->trace_on && !f->trace) {
+        if (cudaMalloc(&f->trace, 2 * sizeof(uint64_t) * std::max<int32_t>(1, plan->dg.d.ntasks)) != cudaSuccess)
+            return TQR_ERR_NOMEM;
+    }
     ExecParams P = base_params(f);
-    cudaError_t e = launch_factor_exec(P, graph_for_launch(plan->dg.d), f->fst, plan->G, plan->smem, true,
-                                       f->stream);
+    P.trace = f->trace_on ? f->trace : nullptr;
+    cudaError_t e = launch_factor_exec(P, graph_for_launch(plan->dg.d), f->fst, plan->G, smem, true, f->stream);
     *out = f;
     return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }
@@ -308,6 +342,30 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
         PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
                     (tree == TQR_PLASMA || tree == TQR_GRASAP) ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
         return run_factor(key, A, stream, out);
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, int precision, void* stream,
+                  tqr_factors** out) {
+    try {
+        int rc = check_common(A, m, n, nb, ib);
+        if (rc != TQR_OK) return rc;
+        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -6;
+        const int p = static_cast<int>((m + nb - 1) / nb);
+        const int q = static_cast<int>((n + nb - 1) / nb);
+        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -7;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
+        if (precision < TQR_FP64 || precision > TQR_TF32) return -8;
+        if (!out) return -10;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
+        PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
+                    (tree == TQR_PLASMA || tree == TQR_GRASAP) ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
+        return run_factor(key, A, stream, out, precision);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
     } catch (...) {
@@ -392,6 +450,44 @@ int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream) {
         f->stream = s;
         return launch_form_t(x, P.d_panels, P.npanels, T_geqrt, T_elim, s) == cudaSuccess ? TQR_OK
                                                                                            : TQR_ERR_CUDA;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_set_trace(tqr_factors* f, int enable) {
+    if (!f) return -1;
+    f->trace_on = enable ? 1 : 0;
+    return TQR_OK;
+}
+
+int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count) {
+    try {
+        if (!f || !f->plan) return -1;
+        if (!count) return -4;
+        const Plan& P = *f->plan;
+        const int64_t nt = P.dg.d.ntasks;
+        *count = nt;
+        if (!f->trace) return TQR_ERR_UNSUPPORTED;     // tracing was not enabled
+        if (cap < nt) return TQR_ERR_CAPACITY;
+        if (!out) return -2;
+        if (cudaStreamSynchronize(f->stream) != cudaSuccess) return TQR_ERR_CUDA;
+        std::vector<uint64_t> raw(2 * static_cast<size_t>(nt));
+        if (cudaMemcpy(raw.data(), f->trace, raw.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TQR_ERR_CUDA;
+        for (int64_t t = 0; t < nt; ++t) {
+            const DevTask& x = P.g.tasks[t];
+            int64_t* o = out + 8 * t;
+            o[0] = x.kind;
+            o[1] = x.i;
+            o[2] = x.piv;
+            o[3] = x.k;
+            o[4] = static_cast<int64_t>(x.j) * 65536 + x.strip;
+            o[5] = static_cast<int64_t>(raw[2 * t]);
+            o[6] = static_cast<int64_t>(raw[2 * t] + (raw[2 * t + 1] & 0x00ffffffffffffffull));
+            o[7] = static_cast<int64_t>(raw[2 * t + 1] >> 56);
+        }
+        return TQR_OK;
     } catch (...) {
         return TQR_ERR_INTERNAL;
     }

@@ -277,12 +277,18 @@ __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* sta
     }
 }
 
+template <int MODE>
+__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, double* Tout, double* scratch);
+template <int G, int MODE, int PREC>
+__device__ void panel_lp_trailing(const Smem& S, const View& top, const View& bot, int nb, int ib, int j0,
+                                  int ncol, const double* Tb64);
+
 // ----------------------------------------------------------------------------
 // Panel kernels: GEQRT(i,k) (MODE GE), TTQRT(i,piv,k) (TT), TSQRT(i,piv,k)
 // (TS).  Blocks of ib columns are factored in turn; after each block its
 // reflectors are applied to the rest of the tile (pair), W columns at a time.
 // ----------------------------------------------------------------------------
-template <int G, int MODE>
+template <int G, int MODE, int PREC>
 __device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* smem) {
     constexpr int W = kThreads / G;
     const Smem S = layout<G>(P, smem);
@@ -310,23 +316,31 @@ __device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* s
             store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
         }
         for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
-        // Trailing update of the columns right of the block.
-        for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
-            __syncthreads();
-            if (MODE == GE) {
-                load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
-            } else {
-                load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-                load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
-            }
-            __syncthreads();
-            apply_block<G, MODE>(S, nb, j0, ib, 1);
-            __syncthreads();
-            if (MODE == GE) {
-                store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
-            } else {
-                store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
-                store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
+        if (PREC != 0) {
+            // T_b in FP64 (Cs is free here), then the trailing columns of the
+            // tile pair on the tensor cores.
+            double* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + (static_cast<int64_t>(k) * P.p + i) * ib * nb;
+            form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
+            panel_lp_trailing<G, MODE, PREC>(S, top, bot, nb, ib, j0, ncol, S.Cs + ib * ib);
+        } else {
+            // Trailing update of the columns right of the block.
+            for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
+                __syncthreads();
+                if (MODE == GE) {
+                    load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
+                } else {
+                    load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
+                    load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
+                }
+                __syncthreads();
+                apply_block<G, MODE>(S, nb, j0, ib, 1);
+                __syncthreads();
+                if (MODE == GE) {
+                    store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
+                } else {
+                    store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+                    store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
+                }
             }
         }
     }
@@ -375,15 +389,367 @@ __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem)
     store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
 }
 
+
+// ----------------------------------------------------------------------------
+// Mixed precision (split-TF32 or TF32 updates, FP64 panels).
+//
+// A panel task also forms, in FP64, the compact-WY factor T_b of each block
+// of ib reflectors (Schreiber-Van Loan forward accumulation) and stores it in
+// the handle's T array.  An update task then applies block b as
+//     C <- C - V_b (T_b^T (V_b^T C))            (GE: UNMQR)
+//     [C_top; C] <- ... with V = [I; V_b]       (TT/TS: TTMQR/TSMQR)
+// with both products on the tensor cores (mma.sync m16n8k8 TF32, FP32
+// accumulation).  Split-TF32 writes each operand x = hi + lo (hi = tf32(x),
+// lo = tf32(x - hi)) and sums hi*hi + hi*lo + lo*hi.  C stays in FP64.
+// ----------------------------------------------------------------------------
+template <int MODE>
+__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, double* Tout, double* scratch) {
+    double* Gm = scratch;             // ib x ib Gram of the block's full reflector vectors
+    double* Tb = scratch + ib * ib;   // ib x ib T
+    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) {
+        const int r = idx % ib, c = idx / ib;
+        double s = 0.0;
+        if (r < c) {
+            const double* vr = S.Vs + r * nb;
+            const double* vc = S.Vs + c * nb;
+            const int jr = j0 + r, jc = j0 + c;
+            if (MODE == GE) {
+                s = vr[jc];                                  // tail of r . unit entry of c
+                for (int x = jc + 1; x < nb; ++x) s = fma(vr[x], vc[x], s);
+            } else {
+                const int hi = (MODE == TT) ? jr + 1 : nb;   // support of the tail of r
+                for (int x = 0; x < hi; ++x) s = fma(vr[x], vc[x], s);
+            }
+        }
+        Gm[idx] = s;
+        Tb[idx] = 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < ib; ++c) {
+        const double tc = S.taus[c];
+        for (int r = threadIdx.x; r < c; r += kThreads) {
+            double s = 0.0;
+            for (int x = r; x < c; ++x) s = fma(Tb[r + x * ib], Gm[x + c * ib], s);
+            Tb[r + c * ib] = -tc * s;
+        }
+        if (threadIdx.x == 0) Tb[c + c * ib] = tc;
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) Tout[idx] = Tb[idx];
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+template <int PREC>
+__device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = (PREC == 1) ? to_tf32(x - __uint_as_float(hi)) : 0u;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// D += A * B with A = ahi + alo, B = bhi + blo (PREC 1: three products; 2: one).
+template <int PREC>
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ahi)[4], const uint32_t (&alo)[4],
+                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    if (PREC == 1) {
+        mma_tf32(d, alo, bh0, bh1);
+        mma_tf32(d, ahi, bl0, bl1);
+    }
+    mma_tf32(d, ahi, bh0, bh1);
+}
+
+struct LpSmem {
+    double* Cs;   // strip nb x W (FP64), leading dimension ldc
+    float* Vf;    // reflector block nb x ib (FP32, unit/zero structure written out), ld ldv
+    float* Tf;    // T_b, ib x ib (FP32), column-major
+    float* Wm;    // W = V^T C (+ C_top): ib x W, row-major (ld W)
+    float* W2;    // T^T W: ib x W, row-major
+    double* Ct;   // top rows (TT/TS): ib x W (FP64), ld ldt
+    int ldc, ldv, ldt;
+};
+
+__host__ __device__ inline int lp_ldv(int nb) { return round16(nb) + 4; }
+
+__host__ __device__ inline int lp_bytes(int nb, int ib, int G) {
+    const int W = kThreads / G;
+    return ldc_of(nb, G) * W * 8 + lp_ldv(nb) * ib * 4 + ib * ib * 4 + 2 * ib * W * 4 + (ib + 1) * W * 8;
+}
+
 template <int G>
+__device__ __forceinline__ LpSmem lp_layout(const ExecParams& P, double* base) {
+    constexpr int W = kThreads / G;
+    LpSmem s;
+    s.ldc = ldc_of(P.nb, G);
+    s.ldv = lp_ldv(P.nb);
+    s.ldt = P.ib + 1;
+    s.Cs = base;
+    s.Ct = s.Cs + s.ldc * W;
+    s.Vf = reinterpret_cast<float*>(s.Ct + s.ldt * W);
+    s.Tf = s.Vf + s.ldv * P.ib;
+    s.Wm = s.Tf + P.ib * P.ib;
+    s.W2 = s.Wm + P.ib * W;
+    return s;
+}
+
+// One block of ib reflectors, staged in S.Vf (FP32, unit/zero structure
+// written out) with its T in S.Tf, applied to the strip in S.Cs (rows
+// [rlo, rhi)) and, for TT/TS, to the top rows in S.Ct:
+//   W = V^T C (+ C_top),  W2 = T^T W,  C_top -= W2,  C -= V W2.
+template <int G, int MODE, int PREC>
+__device__ void lp_apply(const LpSmem& S, int ib, int rlo, int rhi) {
+    constexpr int W = kThreads / G;        // strip width (multiple of 8)
+    constexpr int NNT = W / 8;              // n-tiles of the strip
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int nmt1 = ib / 16;               // m-tiles of W (reflectors)
+    // W = V_b^T C over rows [rlo, rhi): warp w owns m-tile w % nmt1 and the
+    // n-tiles (w / nmt1) + (8 / nmt1) * t.
+    {
+        const int mt = warp % nmt1;
+        const int m0 = mt * 16;
+        constexpr int kMaxAcc = 8;
+        float acc[kMaxAcc][4];
+        const int nstep = 8 / nmt1;
+        int nts = 0;
+        for (int nt = warp / nmt1; nt < NNT; nt += nstep) ++nts;
+#pragma unroll
+        for (int a = 0; a < kMaxAcc; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
+        for (int k0 = rlo; k0 < rhi; k0 += 8) {
+            uint32_t ahi[4], alo[4];
+            split<PREC>(S.Vf[(k0 + tig) + (m0 + gid) * S.ldv], ahi[0], alo[0]);
+            split<PREC>(S.Vf[(k0 + tig) + (m0 + gid + 8) * S.ldv], ahi[1], alo[1]);
+            split<PREC>(S.Vf[(k0 + tig + 4) + (m0 + gid) * S.ldv], ahi[2], alo[2]);
+            split<PREC>(S.Vf[(k0 + tig + 4) + (m0 + gid + 8) * S.ldv], ahi[3], alo[3]);
+#pragma unroll
+            for (int a = 0; a < kMaxAcc; ++a) {
+                if (a < nts) {
+                    const int n0 = (warp / nmt1 + a * nstep) * 8;
+                    uint32_t bh0, bl0, bh1, bl1;
+                    split<PREC>(static_cast<float>(S.Cs[(k0 + tig) + (n0 + gid) * S.ldc]), bh0, bl0);
+                    split<PREC>(static_cast<float>(S.Cs[(k0 + tig + 4) + (n0 + gid) * S.ldc]), bh1, bl1);
+                    mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < kMaxAcc; ++a) {
+            if (a < nts) {
+                const int n0 = (warp / nmt1 + a * nstep) * 8;
+                S.Wm[(m0 + gid) * W + n0 + 2 * tig] = acc[a][0];
+                S.Wm[(m0 + gid) * W + n0 + 2 * tig + 1] = acc[a][1];
+                S.Wm[(m0 + gid + 8) * W + n0 + 2 * tig] = acc[a][2];
+                S.Wm[(m0 + gid + 8) * W + n0 + 2 * tig + 1] = acc[a][3];
+            }
+        }
+    }
+    __syncthreads();
+    // W2 = T^T (W + C_top); C_top -= W2.
+    for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
+        const int a = idx / W, n = idx % W;
+        float s = 0.0f;
+        for (int x = 0; x <= a; ++x) {
+            float w = S.Wm[x * W + n];
+            if (MODE != GE) w += static_cast<float>(S.Ct[x + n * S.ldt]);
+            s = fmaf(S.Tf[x + a * ib], w, s);
+        }
+        S.W2[a * W + n] = s;
+    }
+    __syncthreads();
+    if (MODE != GE)
+        for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
+            const int a = idx / W, n = idx % W;
+            S.Ct[a + n * S.ldt] -= static_cast<double>(S.W2[a * W + n]);
+        }
+    // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...
+    for (int mt = (rlo / 16) + warp; mt < rhi / 16; mt += 8) {
+        const int r0 = mt * 16;
+        for (int nt = 0; nt < NNT; ++nt) {
+            const int n0 = nt * 8;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int k0 = 0; k0 < ib; k0 += 8) {
+                uint32_t ahi[4], alo[4];
+                split<PREC>(S.Vf[(r0 + gid) + (k0 + tig) * S.ldv], ahi[0], alo[0]);
+                split<PREC>(S.Vf[(r0 + gid + 8) + (k0 + tig) * S.ldv], ahi[1], alo[1]);
+                split<PREC>(S.Vf[(r0 + gid) + (k0 + tig + 4) * S.ldv], ahi[2], alo[2]);
+                split<PREC>(S.Vf[(r0 + gid + 8) + (k0 + tig + 4) * S.ldv], ahi[3], alo[3]);
+                uint32_t bh0, bl0, bh1, bl1;
+                split<PREC>(S.W2[(k0 + tig) * W + n0 + gid], bh0, bl0);
+                split<PREC>(S.W2[(k0 + tig + 4) * W + n0 + gid], bh1, bl1);
+                mma3<PREC>(acc, ahi, alo, bh0, bh1, bl0, bl1);
+            }
+            S.Cs[(r0 + gid) + (n0 + 2 * tig) * S.ldc] -= static_cast<double>(acc[0]);
+            S.Cs[(r0 + gid) + (n0 + 2 * tig + 1) * S.ldc] -= static_cast<double>(acc[1]);
+            S.Cs[(r0 + gid + 8) + (n0 + 2 * tig) * S.ldc] -= static_cast<double>(acc[2]);
+            S.Cs[(r0 + gid + 8) + (n0 + 2 * tig + 1) * S.ldc] -= static_cast<double>(acc[3]);
+        }
+    }
+}
+
+template <int G, int MODE, int PREC>
+__device__ void update_task_lp(const ExecParams& P, const DevTask& T, double* smem) {
+    constexpr int W = kThreads / G;
+    const LpSmem S = lp_layout<G>(P, smem);
+    const int nb = P.nb, ib = P.ib;
+    const View vt = tile_view(P, T.i, T.k);
+    const int64_t toff = (static_cast<int64_t>(T.k) * P.p + T.i);
+    const double* Tsrc = ((MODE == GE) ? P.T_ge : P.T_el) + toff * ib * nb;
+    const int c0 = T.strip * W;
+    const View bot = tile_view(P, T.i, T.j);
+    const View top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
+    load_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W);
+    for (int j0 = 0; j0 < nb; j0 += ib) {
+        // Rows of C touched by this block's reflectors.
+        const int rlo = (MODE == GE) ? j0 : 0;
+        const int rhi = (MODE == TT) ? j0 + ib : nb;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < (rhi - rlo) * ib; idx += kThreads) {
+            const int r = rlo + idx % (rhi - rlo);
+            const int jj = idx / (rhi - rlo);
+            const int j = j0 + jj;
+            float v = 0.0f;
+            if (MODE == GE) {
+                if (r == j) v = 1.0f;
+                else if (r > j && r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
+            } else if (MODE == TT) {
+                if (r <= j && r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
+            } else {
+                if (r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
+            }
+            S.Vf[r + jj * S.ldv] = v;
+        }
+        for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads)
+            S.Tf[idx] = static_cast<float>(__ldcg(Tsrc + static_cast<int64_t>(j0) * ib + idx));
+        if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
+        __syncthreads();
+        lp_apply<G, MODE, PREC>(S, ib, rlo, rhi);
+        if (MODE != GE) {
+            __syncthreads();
+            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+        }
+    }
+    __syncthreads();
+    store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
+}
+
+// Shared memory of a panel task's low-precision trailing update: Vf overlays
+// the FP64 reflector block (converted after it was written back); Tf, Wm, W2
+// follow Vf when they fit in that region, else they follow tau.
+__host__ __device__ inline bool panel_lp_fits(int nb, int ib, int G) {
+    const int W = kThreads / G;
+    return (lp_ldv(nb) * ib + ib * ib + 2 * ib * W) * 4 <= nb * ib * 8;
+}
+
+__host__ __device__ inline int panel_lp_extra_bytes(int nb, int ib, int G) {
+    const int W = kThreads / G;
+    return panel_lp_fits(nb, ib, G) ? 0 : (ib * ib + 2 * ib * W) * 4;
+}
+
+// After a panel block is factored (Vs, taus) and its T is in Tb64 (FP64,
+// ib x ib, in the strip area): the trailing columns [j0+ib, ncol) of the tile
+// pair get the block on the tensor cores.
+template <int G, int MODE, int PREC>
+__device__ void panel_lp_trailing(const Smem& S, const View& top, const View& bot, int nb, int ib, int j0,
+                                  int ncol, const double* Tb64) {
+    constexpr int W = kThreads / G;
+    constexpr int kMaxReg = 64;             // nb * ib <= 256 * 64 values over 256 threads
+    LpSmem L;
+    L.Cs = S.Cs;
+    L.ldc = S.ldc;
+    L.Ct = S.Ct;
+    L.ldt = S.ldt;
+    L.ldv = lp_ldv(nb);
+    L.Vf = reinterpret_cast<float*>(S.Vs);
+    if (panel_lp_fits(nb, ib, G)) L.Tf = L.Vf + L.ldv * ib;
+    else L.Tf = reinterpret_cast<float*>(S.taus + ib);
+    L.Wm = L.Tf + ib * ib;
+    L.W2 = L.Wm + ib * W;
+    const int rlo = (MODE == GE) ? j0 : 0;
+    const int rhi = (MODE == TT) ? j0 + ib : nb;
+    const int nv = (rhi - rlo) * ib;
+    // Vs (FP64) -> registers -> Vf (FP32) in place; T (FP64) -> registers.
+    float buf[kMaxReg];
+    float tb[kMaxReg / 4 + 1];
+#pragma unroll
+    for (int e = 0; e < kMaxReg; ++e) {
+        const int idx = threadIdx.x + e * kThreads;
+        float v = 0.0f;
+        if (idx < nv) {
+            const int r = rlo + idx % (rhi - rlo);
+            const int jj = idx / (rhi - rlo);
+            const int j = j0 + jj;
+            const double x = S.Vs[r + jj * nb];
+            if (MODE == GE) v = (r == j) ? 1.0f : (r > j ? static_cast<float>(x) : 0.0f);
+            else if (MODE == TT) v = (r <= j) ? static_cast<float>(x) : 0.0f;
+            else v = static_cast<float>(x);
+        }
+        buf[e] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxReg / 4 + 1; ++e) {
+        const int idx = threadIdx.x + e * kThreads;
+        tb[e] = (idx < ib * ib) ? static_cast<float>(Tb64[idx]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kMaxReg; ++e) {
+        const int idx = threadIdx.x + e * kThreads;
+        if (idx < nv) {
+            const int r = rlo + idx % (rhi - rlo);
+            const int jj = idx / (rhi - rlo);
+            L.Vf[r + jj * L.ldv] = buf[e];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxReg / 4 + 1; ++e) {
+        const int idx = threadIdx.x + e * kThreads;
+        if (idx < ib * ib) L.Tf[idx] = tb[e];
+    }
+    for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
+        __syncthreads();
+        if (MODE == GE) {
+            load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
+        } else {
+            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
+            load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
+        }
+        __syncthreads();
+        lp_apply<G, MODE, PREC>(L, ib, rlo, rhi);
+        __syncthreads();
+        if (MODE == GE) {
+            store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
+        } else {
+            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+            store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
+        }
+    }
+}
+
+template <int G, int MODE, int PREC>
+__device__ __forceinline__ void update_any(const ExecParams& P, const DevTask& T, double* smem) {
+    if (PREC != 0 && !P.B) update_task_lp<G, MODE, (PREC != 0 ? PREC : 1)>(P, T, smem);
+    else update_task<G, MODE>(P, T, smem);
+}
+
+template <int G, int PREC>
 __device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
     switch (T.kind) {
-        case GEQRT: panel_task<G, GE>(P, T.i, -1, T.k, smem); break;
-        case TTQRT: panel_task<G, TT>(P, T.i, T.piv, T.k, smem); break;
-        case TSQRT: panel_task<G, TS>(P, T.i, T.piv, T.k, smem); break;
-        case UNMQR: update_task<G, GE>(P, T, smem); break;
-        case TTMQR: update_task<G, TT>(P, T, smem); break;
-        case TSMQR: update_task<G, TS>(P, T, smem); break;
+        case GEQRT: panel_task<G, GE, PREC>(P, T.i, -1, T.k, smem); break;
+        case TTQRT: panel_task<G, TT, PREC>(P, T.i, T.piv, T.k, smem); break;
+        case TSQRT: panel_task<G, TS, PREC>(P, T.i, T.piv, T.k, smem); break;
+        case UNMQR: update_any<G, GE, PREC>(P, T, smem); break;
+        case TTMQR: update_any<G, TT, PREC>(P, T, smem); break;
+        case TSMQR: update_any<G, TS, PREC>(P, T, smem); break;
         default: set_status(P.status, TQR_ERR_INTERNAL); break;
     }
 }
@@ -416,7 +782,7 @@ __device__ void release_successors(const ExecParams& P, int t) {
     }
 }
 
-template <int G>
+template <int G, int PREC>
 __global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
     extern __shared__ __align__(16) double smem[];
     __shared__ int s_task;
@@ -449,8 +815,16 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
         const int t = s_task;
         if (t < 0) return;
         const DevTask T = P.tasks[t];
-        run_task<G>(P, T, smem);
+        uint64_t t_begin = 0;
+        if (P.trace && threadIdx.x == 0) t_begin = globaltimer();
+        run_task<G, PREC>(P, T, smem);
         __syncthreads();
+        if (P.trace && threadIdx.x == 0) {
+            uint32_t sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            P.trace[2 * t] = t_begin;
+            P.trace[2 * t + 1] = ((globaltimer() - t_begin) & 0x00ffffffffffffffull) | (static_cast<uint64_t>(sm) << 56);
+        }
         if (threadIdx.x < 32) release_successors(P, t);
     }
 }
@@ -533,6 +907,17 @@ __global__ void form_t_kernel(ExecParams P, const int32_t* panels, double* T_ge,
 // ----------------------------------------------------------------------------
 int strip_width(int G) { return kThreads / G; }
 
+int lp_smem_bytes(int nb, int ib, int G) {
+    const int panel = smem_doubles(nb, ib, G) * 8 + panel_lp_extra_bytes(nb, ib, G);
+    const int upd = lp_bytes(nb, ib, G);
+    return panel > upd ? panel : upd;
+}
+
+bool lp_supported(int nb, int ib, int G) {
+    const int W = kThreads / G;
+    return nb % 16 == 0 && ib % 16 == 0 && 8 % (ib / 16) == 0 && W % 8 == 0 && W / 8 <= 8;
+}
+
 bool choose_layout(int nb, int ib, int* G, int* smem_bytes) {
     int dev = 0, maxsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -560,12 +945,22 @@ int device_sm_count() {
     return n;
 }
 
+template <int G, int PREC>
+static cudaError_t launch_gp(const ExecParams& P, int smem, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(exec_kernel<G, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    exec_kernel<G, PREC><<<grid, kThreads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
 template <int G>
 static cudaError_t launch_g(const ExecParams& P, int smem, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(exec_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    exec_kernel<G><<<grid, kThreads, smem, s>>>(P);
-    return cudaGetLastError();
+    switch (P.B ? 0 : P.prec) {      // apply graphs always run the FP64 kernels
+        case 0: return launch_gp<G, 0>(P, smem, grid, s);
+        case 1: return launch_gp<G, 1>(P, smem, grid, s);
+        case 2: return launch_gp<G, 2>(P, smem, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G, int smem,

@@ -1,0 +1,296 @@
+// Least squares min ||A x - b|| on top of the tiled QR (the paper's motivating
+// use, Section 1), with an optional low-precision factorization refined in
+// FP64:
+//   1. factor a copy of A (FP64, or FP64 panels + split-TF32 / TF32 updates);
+//   2. c = Q^T b with the stored reflectors applied in FP64;
+//   3. Rinv = R^-1 (explicit FP64 inverse of the computed R, one warp per
+//      column), x = Rinv c[0:n];
+//   4. low precision: corrected semi-normal-equation refinement in FP64,
+//        r = b - A x,  s = A^T r,  x += Rinv Rinv^T s,
+//      until the backward error ||A^T r|| / (||A||_F ||r||) reaches tol; if it
+//      stops decreasing, R-preconditioned CGLS (min ||A Rinv z - b||, x =
+//      Rinv z) continues from the current x.
+// Every residual, product with A and the solution are FP64.
+#include "tqr_internal.h"
+#include "../../include/tqr.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kT = 256;
+
+// y = b - A x  (A: m x n column-major, lda).  One thread per row; x staged
+// in shared memory in chunks.
+__global__ void resid_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                             const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y) {
+    __shared__ double xs[1024];
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t c0 = 0; c0 < n; c0 += 1024) {
+        const int64_t cn = std::min<int64_t>(1024, n - c0);
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < cn; t += blockDim.x) xs[t] = x[c0 + t];
+        __syncthreads();
+        if (r < m) {
+            const double* a = A + r + c0 * lda;
+            int64_t c = 0;
+            for (; c + 1 < cn; c += 2) {
+                acc0 = fma(a[c * lda], xs[c], acc0);
+                acc1 = fma(a[(c + 1) * lda], xs[c + 1], acc1);
+            }
+            if (c < cn) acc0 = fma(a[c * lda], xs[c], acc0);
+        }
+    }
+    if (r < m) y[r] = b[r] - (acc0 + acc1);
+}
+
+__device__ __forceinline__ double warp_reduce(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// s = A^T r: one warp per column.
+__global__ void atr_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                           const double* __restrict__ r, double* __restrict__ s) {
+    const int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    const double* a = A + c * lda;
+    double acc = 0.0;
+    for (int64_t i = lane; i < m; i += 32) acc = fma(a[i], r[i], acc);
+    acc = warp_reduce(acc);
+    if (lane == 0) s[c] = acc;
+}
+
+// Ginv = R^-1 for R = triu(Af[0:n, 0:n]) (lda): one warp per column c solves
+// R g = e_c by column-oriented back substitution, g kept in column c of Ginv.
+__global__ void tri_inverse_kernel(const double* __restrict__ R, int64_t lda, int64_t n, double* __restrict__ Gi,
+                                   int64_t ldg) {
+    const int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    double* g = Gi + c * ldg;
+    for (int64_t i = lane; i < n; i += 32) g[i] = (i == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int64_t j = c; j >= 0; --j) {
+        double gj = 0.0;
+        if (lane == (j & 31)) {
+            gj = g[j] / R[j + j * lda];
+            g[j] = gj;
+        }
+        gj = __shfl_sync(0xffffffffu, gj, static_cast<int>(j & 31));
+        const double* rc = R + j * lda;
+        for (int64_t i = lane; i < j; i += 32) g[i] = fma(-rc[i], gj, g[i]);
+        __syncwarp();
+    }
+}
+
+// y = G v (trans = 0) or G^T v (trans = 1) for upper-triangular G (n x n, ldg).
+__global__ void trmv_kernel(const double* __restrict__ G, int64_t ldg, int64_t n, const double* __restrict__ v,
+                            double* __restrict__ y, int trans) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    if (w >= n) return;
+    double acc = 0.0;
+    if (trans) {            // y[w] = sum_{i <= w} G[i, w] v[i]
+        const double* g = G + w * ldg;
+        for (int64_t i = lane; i <= w; i += 32) acc = fma(g[i], v[i], acc);
+    } else {                // y[w] = sum_{j >= w} G[w, j] v[j]
+        for (int64_t j = w + lane; j < n; j += 32) acc = fma(G[w + j * ldg], v[j], acc);
+    }
+    acc = warp_reduce(acc);
+    if (lane == 0) y[w] = acc;
+}
+
+// out[0] += sum x[i]*y[i] (block partials via atomics on a zeroed slot).
+__global__ void dot_kernel(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* out) {
+    __shared__ double part[kT / 32];
+    double acc = 0.0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        acc = fma(x[i], y[i], acc);
+    acc = warp_reduce(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x / 32] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < blockDim.x / 32 ? part[threadIdx.x] : 0.0;
+        v = warp_reduce(v);
+        if (threadIdx.x == 0) atomicAdd(out, v);
+    }
+}
+
+// y = a*x + y
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        y[i] = fma(a, x[i], y[i]);
+}
+
+// p = s + beta p
+__global__ void xpby_kernel(const double* __restrict__ s, double beta, double* __restrict__ p, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        p[i] = fma(beta, p[i], s[i]);
+}
+
+struct Ws {
+    double *Af = nullptr, *Gi = nullptr, *c = nullptr, *r = nullptr, *q = nullptr;
+    double *s = nullptr, *u = nullptr, *d = nullptr, *t = nullptr, *pv = nullptr, *sc = nullptr;
+    ~Ws() {
+        for (double* p : {Af, Gi, c, r, q, s, u, d, t, pv, sc}) cudaFree(p);
+    }
+};
+
+struct Solver {
+    const double* A;
+    int64_t m, n;
+    const double* b;
+    double* x;
+    cudaStream_t st;
+    Ws w;
+    int blocks = 1024;
+
+    int grid_rows() const { return static_cast<int>((m + kT - 1) / kT); }
+    int grid_cols(int64_t cols) const { return static_cast<int>((cols + kT / 32 - 1) / (kT / 32)); }
+
+    double dot(const double* a, const double* b2, int64_t len) {
+        cudaMemsetAsync(w.sc, 0, sizeof(double), st);
+        dot_kernel<<<std::min<int64_t>(blocks, (len + kT - 1) / kT), kT, 0, st>>>(a, b2, len, w.sc);
+        double h = 0.0;
+        cudaMemcpyAsync(&h, w.sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        return h;
+    }
+    void resid() { resid_kernel<<<grid_rows(), kT, 0, st>>>(A, m, m, n, x, b, w.r); }   // r = b - A x
+    void atr(const double* r, double* s) { atr_kernel<<<grid_cols(n), kT, 0, st>>>(A, m, m, n, r, s); }
+    void gmul(const double* v, double* y, int trans) {
+        trmv_kernel<<<grid_cols(n), kT, 0, st>>>(w.Gi, n, n, v, y, trans);
+    }
+    int nblk(int64_t len) const { return static_cast<int>(std::min<int64_t>(blocks, (len + kT - 1) / kT)); }
+};
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+extern "C" int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b, double* x, int nb, int ib,
+                         int tree, int BS, int precision, double tol, int maxit, void* stream,
+                         tqr_lstsq_info* info) {
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (n < 1 || n > m) return -3;
+    if (!b) return -4;
+    if (!x) return -5;
+    if (precision < TQR_FP64 || precision > TQR_TF32) return -10;
+    if (maxit < 0) return -12;
+    tqr_lstsq_info local{};
+    tqr_lstsq_info& I = info ? *info : local;
+    I = tqr_lstsq_info{};
+    Solver S;
+    S.A = A;
+    S.m = m;
+    S.n = n;
+    S.b = b;
+    S.x = x;
+    S.st = static_cast<cudaStream_t>(stream);
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t mn = static_cast<size_t>(m) * n;
+    if (cudaMalloc(&S.w.Af, mn * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.Gi, static_cast<size_t>(n) * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.c, m * sizeof(double)) != cudaSuccess || cudaMalloc(&S.w.r, m * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.q, m * sizeof(double)) != cudaSuccess || cudaMalloc(&S.w.s, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.u, n * sizeof(double)) != cudaSuccess || cudaMalloc(&S.w.d, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.t, n * sizeof(double)) != cudaSuccess || cudaMalloc(&S.w.pv, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.w.sc, sizeof(double)) != cudaSuccess)
+        return TQR_ERR_NOMEM;
+    cudaMemcpyAsync(S.w.Af, A, mn * sizeof(double), cudaMemcpyDeviceToDevice, S.st);
+    tqr_factors* f = nullptr;
+    int rc = tqr_factor_ex(S.w.Af, m, n, nb, ib, tree, BS, precision, stream, &f);
+    if (rc != TQR_OK) return rc;
+    cudaMemcpyAsync(S.w.c, b, m * sizeof(double), cudaMemcpyDeviceToDevice, S.st);
+    rc = tqr_apply_qt(f, S.w.c, m, 1, stream);
+    if (rc == TQR_OK) rc = tqr_sync(f);
+    if (rc != TQR_OK) {
+        tqr_free(f);
+        return rc;
+    }
+    I.factor_seconds = seconds_since(t0);
+    auto t1 = std::chrono::steady_clock::now();
+    tri_inverse_kernel<<<S.grid_cols(n), kT, 0, S.st>>>(S.w.Af, m, n, S.w.Gi, n);
+    S.gmul(S.w.c, x, 0);                                   // x = Rinv c[0:n]
+    const double normA = std::sqrt(S.dot(A, A, static_cast<int64_t>(mn)));
+    auto backward = [&](double* rnorm) {                   // r, s = A^T r, eta
+        S.resid();
+        S.atr(S.w.r, S.w.s);
+        const double rr = S.dot(S.w.r, S.w.r, m);
+        const double ss = S.dot(S.w.s, S.w.s, n);
+        *rnorm = std::sqrt(rr);
+        return (rr > 0.0) ? std::sqrt(ss) / (normA * std::sqrt(rr)) : 0.0;
+    };
+    double rnorm = 0.0;
+    double eta = backward(&rnorm);
+    I.refine_iterations = 0;
+    I.cgls_iterations = 0;
+    if (precision != TQR_FP64) {
+        double prev = eta;
+        while (eta > tol && I.refine_iterations < maxit) {
+            S.gmul(S.w.s, S.w.u, 1);                       // u = Rinv^T s
+            S.gmul(S.w.u, S.w.d, 0);                       // d = Rinv u
+            axpy_kernel<<<S.nblk(n), kT, 0, S.st>>>(1.0, S.w.d, x, n);
+            ++I.refine_iterations;
+            eta = backward(&rnorm);
+            if (eta > 0.5 * prev) break;                   // not contracting: hand over to CGLS
+            prev = eta;
+        }
+        if (eta > tol && I.refine_iterations < maxit) {
+            // CGLS on the correction problem min ||r - (A Rinv) z||, x += Rinv z.
+            // c (Q^T b) is no longer needed: it becomes the zero vector so
+            // that resid(t, c) = -A t.
+            cudaMemsetAsync(S.w.c, 0, m * sizeof(double), S.st);
+            S.gmul(S.w.s, S.w.u, 1);                       // u = Rinv^T A^T r
+            cudaMemcpyAsync(S.w.pv, S.w.u, n * sizeof(double), cudaMemcpyDeviceToDevice, S.st);
+            double gamma = S.dot(S.w.u, S.w.u, n);
+            while (eta > tol && I.refine_iterations + I.cgls_iterations < maxit && gamma > 0.0) {
+                S.gmul(S.w.pv, S.w.t, 0);                  // t = Rinv p
+                resid_kernel<<<S.grid_rows(), kT, 0, S.st>>>(A, m, m, n, S.w.t, S.w.c, S.w.q);  // q = -A t
+                const double qq = S.dot(S.w.q, S.w.q, m);
+                if (qq <= 0.0) break;
+                const double alpha = gamma / qq;
+                axpy_kernel<<<S.nblk(n), kT, 0, S.st>>>(alpha, S.w.t, x, n);      // x += alpha t
+                ++I.cgls_iterations;
+                if (I.cgls_iterations % 4 == 0) {
+                    eta = backward(&rnorm);                 // true FP64 residual replaces r
+                } else {
+                    axpy_kernel<<<S.nblk(m), kT, 0, S.st>>>(alpha, S.w.q, S.w.r, m);  // r -= alpha A t
+                    S.atr(S.w.r, S.w.s);
+                    const double rr = S.dot(S.w.r, S.w.r, m), ss = S.dot(S.w.s, S.w.s, n);
+                    rnorm = std::sqrt(rr);
+                    eta = rr > 0.0 ? std::sqrt(ss) / (normA * std::sqrt(rr)) : 0.0;
+                }
+                S.gmul(S.w.s, S.w.u, 1);                   // u = Rinv^T A^T r
+                const double gnew = S.dot(S.w.u, S.w.u, n);
+                xpby_kernel<<<S.nblk(n), kT, 0, S.st>>>(S.w.u, gnew / gamma, S.w.pv, n);
+                gamma = gnew;
+            }
+            eta = backward(&rnorm);
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(S.st);
+    I.solve_seconds = seconds_since(t1);
+    I.backward_error = eta;
+    I.residual_norm = rnorm;
+    I.converged = (precision == TQR_FP64 || eta <= tol) ? 1 : 0;
+    I.status = tqr_sync(f);
+    tqr_free(f);
+    if (e != cudaSuccess) return TQR_ERR_CUDA;
+    return I.status;
+}

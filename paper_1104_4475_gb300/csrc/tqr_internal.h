@@ -94,15 +94,23 @@ struct ExecParams {
     double* tau_el;                              // tau of TTQRT/TSQRT zeroing (i,k)
     double* B; int64_t ldb, nrhs;                // right-hand side (apply graphs), else null
     int trans;                                   // 1: apply Q^T, 0: apply Q
+    int prec;                                    // 0: FP64 updates, 1: split-TF32 (3 pass), 2: TF32
+    double* T_ge;                                // compact-WY T blocks (prec != 0): ib x nb per tile
+    double* T_el;
     const DevTask* tasks; const int32_t* succ_ptr; const int32_t* succ;
     int32_t* deps; int32_t* queue; uint32_t* ctr; int32_t* status;
     int32_t ntasks;
     uint64_t timeout_ns;                         // limit for any single wait
+    uint64_t* trace;                             // optional: 2 per task (start, duration | sm << 56)
 };
 
 // Row groups per strip column (G) and dynamic shared memory for (nb, ib);
 // returns false if no layout fits.
 bool choose_layout(int nb, int ib, int* G, int* smem_bytes);
+// Shared memory the low-precision update kernels need for (nb, ib, G), and
+// whether the low-precision path supports (nb, ib) at all.
+int lp_smem_bytes(int nb, int ib, int G);
+bool lp_supported(int nb, int ib, int G);
 int strip_width(int G);
 int device_sm_count();
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,

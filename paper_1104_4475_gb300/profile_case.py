@@ -24,6 +24,7 @@ def main(argv=None):
     ap.add_argument("--BS", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 split-TF32, 2 TF32 updates")
     a = ap.parse_args(argv)
     import torch
     from . import tqr, build, workloads
@@ -37,13 +38,13 @@ def main(argv=None):
         A.copy_(A0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        f = tqr.tqr_factor(A, a.nb, a.ib, tree, a.BS, reuse=f)
+        f = tqr.tqr_factor_ex(A, a.nb, a.ib, tree, a.BS, a.precision, reuse=f)
         e1.record()
         tqr.tqr_sync(f)
         t = e0.elapsed_time(e1) / 1e3
         info = f.info()
-        print("%s m=%d n=%d nb=%d ib=%d tree=%s tasks=%d cp=%d: %.3f ms, %.1f GFLOP/s"
-              % ("warmup" if r < a.warmup else "rep", a.m, n, a.nb, a.ib, a.tree, info["n_device_tasks"],
+        print("%s m=%d n=%d nb=%d ib=%d tree=%s prec=%d tasks=%d cp=%d: %.3f ms, %.1f GFLOP/s"
+              % ("warmup" if r < a.warmup else "rep", a.m, n, a.nb, a.ib, a.tree, a.precision, info["n_device_tasks"],
                  info["critical_path"], 1e3 * t, info["flops"] / t / 1e9), flush=True)
     f.free()
     return 0

@@ -37,6 +37,16 @@ class TqrError(RuntimeError):
         super().__init__("%s: %s (%d)" % (where, tqr_strerror(code), code))
 
 
+TQR_FP64, TQR_SPLIT_TF32, TQR_TF32 = 0, 1, 2
+
+
+class tqr_lstsq_info(ctypes.Structure):
+    _fields_ = [("refine_iterations", ctypes.c_int32), ("cgls_iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("status", ctypes.c_int32), ("backward_error", ctypes.c_double),
+                ("residual_norm", ctypes.c_double), ("factor_seconds", ctypes.c_double),
+                ("solve_seconds", ctypes.c_double)]
+
+
 class tqr_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
                 ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("tree", ctypes.c_int32), ("BS", ctypes.c_int32),
@@ -61,6 +71,9 @@ def lib():
         sig = {
             "tqr_factor": [vp, i64, i64, i32, i32, i32, i32, vp, ctypes.POINTER(vp)],
             "tqr_factor_list": [vp, i64, i64, i32, i32, pi32, i64, i32, vp, ctypes.POINTER(vp)],
+            "tqr_factor_ex": [vp, i64, i64, i32, i32, i32, i32, i32, vp, ctypes.POINTER(vp)],
+            "tqr_lstsq": [vp, i64, i64, vp, vp, i32, i32, i32, i32, i32, ctypes.c_double, i32, vp,
+                          ctypes.POINTER(tqr_lstsq_info)],
             "tqr_apply_qt": [vp, vp, i64, i64, vp],
             "tqr_apply_q": [vp, vp, i64, i64, vp],
             "tqr_form_t": [vp, vp, vp, vp],
@@ -71,6 +84,8 @@ def lib():
             "tqr_validate_list": [i32, i32, pi32, i64],
             "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
             "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
+            "tqr_set_trace": [vp, i32],
+            "tqr_get_trace": [vp, pi64, i64, pi64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -167,6 +182,35 @@ def tqr_factor(A, nb, ib, tree, BS=1, stream=None, reuse=None):
     return Factors(h.value, A)
 
 
+def tqr_factor_ex(A, nb, ib, tree, BS=1, precision=TQR_FP64, stream=None, reuse=None):
+    """tqr_factor with a choice of update arithmetic (TQR_FP64, TQR_SPLIT_TF32, TQR_TF32)."""
+    ptr, ld = _colmajor_ptr(A, "A")
+    m, n = A.shape
+    if ld != m:
+        raise ValueError("A must have leading dimension m")
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    _check(lib().tqr_factor_ex(ptr, m, n, nb, ib, int(tree), BS, int(precision), _stream(stream),
+                               ctypes.byref(h)), "tqr_factor_ex")
+    if reuse is not None and h.value == reuse.ptr:
+        reuse.A = A
+        return reuse
+    return Factors(h.value, A)
+
+
+def tqr_lstsq(A, b, x, nb, ib, tree, BS=1, precision=TQR_FP64, tol=0.0, maxit=50, stream=None):
+    """min ||A x - b||: A (m x n column-major CUDA tensor, unchanged), b (m) and
+    x (n, output) CUDA float64 tensors.  Returns the info as a dict."""
+    ptr, ld = _colmajor_ptr(A, "A")
+    m, n = A.shape
+    if ld != m:
+        raise ValueError("A must have leading dimension m")
+    info = tqr_lstsq_info()
+    rc = lib().tqr_lstsq(ptr, m, n, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nb, ib,
+                         int(tree), BS, int(precision), float(tol), int(maxit), _stream(stream), ctypes.byref(info))
+    _check(rc, "tqr_lstsq")
+    return {k: getattr(info, k) for k, _ in tqr_lstsq_info._fields_}
+
+
 def tqr_factor_list(A, nb, ib, elims, ts=False, stream=None, reuse=None):
     """QR with a caller-given elimination list of 0-based (i, piv, k)."""
     ptr, ld = _colmajor_ptr(A, "A")
@@ -201,6 +245,22 @@ def tqr_form_t(f, T_geqrt=None, T_elim=None, stream=None):
     def p(t):
         return ctypes.c_void_p(t.data_ptr() if t is not None else None)
     _check(lib().tqr_form_t(ctypes.c_void_p(f.ptr), p(T_geqrt), p(T_elim), _stream(stream)), "tqr_form_t")
+
+
+def tqr_set_trace(f, enable=True):
+    _check(lib().tqr_set_trace(ctypes.c_void_p(f.ptr), 1 if enable else 0), "tqr_set_trace")
+
+
+def tqr_get_trace(f):
+    """(ntasks, 8) int64: kind, i, piv, k, j*65536+strip, start ns, end ns, SM."""
+    cnt = ctypes.c_int64(0)
+    rc = lib().tqr_get_trace(ctypes.c_void_p(f.ptr), None, 0, ctypes.byref(cnt))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_get_trace")
+    out = np.zeros((max(1, cnt.value), 8), dtype=np.int64)
+    _check(lib().tqr_get_trace(ctypes.c_void_p(f.ptr), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               out.shape[0], ctypes.byref(cnt)), "tqr_get_trace")
+    return out[: cnt.value]
 
 
 def tqr_sync(f, raise_on_error=True):
