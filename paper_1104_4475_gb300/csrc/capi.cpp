@@ -201,8 +201,10 @@ struct tqr_factors {
     double* tau_el = nullptr;
     int32_t* status = nullptr;
     ExecState fst, ast;
-    double* T_ge = nullptr;      // compact-WY T blocks (low-precision factorizations)
-    double* T_el = nullptr;
+    float* T_ge = nullptr;       // compact-WY T blocks, FP32 (low-precision factorizations)
+    float* T_el = nullptr;
+    float* V_ge = nullptr;       // reflectors in FP32 with unit/zero structure (same)
+    float* V_el = nullptr;
     int prec = 0;
     uint64_t* trace = nullptr;   // per-task (start, duration | sm << 56) when tracing
     int trace_on = 0;
@@ -216,6 +218,8 @@ struct tqr_factors {
         cudaFree(tau_el);
         cudaFree(T_ge);
         cudaFree(T_el);
+        cudaFree(V_ge);
+        cudaFree(V_el);
         cudaFree(trace);
         cudaFree(status);
         cudaFree(own_A);
@@ -251,6 +255,8 @@ static ExecParams base_params(const tqr_factors* f) {
     x.prec = f->prec;
     x.T_ge = f->T_ge;
     x.T_el = f->T_el;
+    x.V_ge = f->V_ge;
+    x.V_el = f->V_el;
     x.trace = nullptr;
     x.timeout_ns = timeout_ns(lapack_flops(P.key.m, P.key.n));
     return x;
@@ -293,8 +299,11 @@ static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors**
     }
     if (prec != 0 && !f->T_ge) {
         const size_t nt = static_cast<size_t>(plan->p) * plan->q * key.ib * key.nb;
-        if (cudaMalloc(&f->T_ge, nt * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&f->T_el, nt * sizeof(double)) != cudaSuccess) {
+        const size_t nv = static_cast<size_t>(plan->p) * plan->q * key.nb * key.nb;
+        if (cudaMalloc(&f->T_ge, nt * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&f->T_el, nt * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&f->V_ge, nv * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&f->V_el, nv * sizeof(float)) != cudaSuccess) {
             if (f != *out) delete f;
             return TQR_ERR_NOMEM;
         }

@@ -278,10 +278,10 @@ __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* sta
 }
 
 template <int MODE>
-__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, double* Tout, double* scratch);
+__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch);
 template <int G, int MODE, int PREC>
-__device__ void panel_lp_trailing(const Smem& S, const View& top, const View& bot, int nb, int ib, int j0,
-                                  int ncol, const double* Tb64);
+__device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
+                                  int ncol, double* smem);
 
 // ----------------------------------------------------------------------------
 // Panel kernels: GEQRT(i,k) (MODE GE), TTQRT(i,piv,k) (TT), TSQRT(i,piv,k)
@@ -319,9 +319,19 @@ __device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* s
         if (PREC != 0) {
             // T_b in FP64 (Cs is free here), then the trailing columns of the
             // tile pair on the tensor cores.
-            double* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + (static_cast<int64_t>(k) * P.p + i) * ib * nb;
+            const int64_t tile = static_cast<int64_t>(k) * P.p + i;
+            float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
+            float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
+            for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
+                const int r = idx % nb, jj = idx / nb, j = j0 + jj;
+                float v;
+                if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * nb]));
+                else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * nb]) : 0.0f;
+                else v = static_cast<float>(S.Vs[r + jj * nb]);
+                Vdst[r + static_cast<int64_t>(j) * nb] = v;
+            }
             form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
-            panel_lp_trailing<G, MODE, PREC>(S, top, bot, nb, ib, j0, ncol, S.Cs + ib * ib);
+            panel_lp_trailing<G, MODE, PREC>(P, i, k, top, bot, j0, ncol, smem);
         } else {
             // Trailing update of the columns right of the block.
             for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
@@ -403,7 +413,7 @@ __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem)
 // lo = tf32(x - hi)) and sums hi*hi + hi*lo + lo*hi.  C stays in FP64.
 // ----------------------------------------------------------------------------
 template <int MODE>
-__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, double* Tout, double* scratch) {
+__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch) {
     double* Gm = scratch;             // ib x ib Gram of the block's full reflector vectors
     double* Tb = scratch + ib * ib;   // ib x ib T
     for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) {
@@ -435,19 +445,7 @@ __device__ void form_t_block(const Smem& S, int nb, int j0, int ib, double* Tout
         if (threadIdx.x == 0) Tb[c + c * ib] = tc;
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) Tout[idx] = Tb[idx];
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-template <int PREC>
-__device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
-    hi = to_tf32(x);
-    lo = (PREC == 1) ? to_tf32(x - __uint_as_float(hi)) : 0u;
+    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) Tout[idx] = static_cast<float>(Tb[idx]);
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -469,269 +467,263 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ahi)[4], co
     mma_tf32(d, ahi, bh0, bh1);
 }
 
-struct LpSmem {
-    double* Cs;   // strip nb x W (FP64), leading dimension ldc
-    float* Vf;    // reflector block nb x ib (FP32, unit/zero structure written out), ld ldv
-    float* Tf;    // T_b, ib x ib (FP32), column-major
-    float* Wm;    // W = V^T C (+ C_top): ib x W, row-major (ld W)
-    float* W2;    // T^T W: ib x W, row-major
-    double* Ct;   // top rows (TT/TS): ib x W (FP64), ld ldt
-    int ldc, ldv, ldt;
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// TF32 split by truncation on the integer pipe: hi keeps the top 19 bits of x,
+// lo the top 19 bits of x - hi (exact in FP32).  PREC 2: hi only.
+template <int PREC>
+__device__ __forceinline__ void split_t(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = (PREC == 1) ? (__float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u) : 0u;
+}
+
+// Layout of an update task in low precision: the strip of C and the strip of
+// the top tile (TT/TS) in FP32, two buffers of the FP32 reflector block and of
+// its T, and W / T^T W.
+struct Lp2 {
+    float* Cf;
+    float* Ctf;
+    float* Vb[2];
+    float* Tb[2];
+    float* Wm;
+    float* W2;
+    int ldc, ldv, ldw;
 };
 
-__host__ __device__ inline int lp_ldv(int nb) { return round16(nb) + 4; }
-
-__host__ __device__ inline int lp_bytes(int nb, int ib, int G) {
+__host__ __device__ inline int lp2_ldc(int nb) { return (nb + 31) / 32 * 32 + 4; }
+__host__ __device__ inline int lp2_ldv(int nb) { return (nb + 15) / 16 * 16 + 4; }
+__host__ __device__ inline int lp2_bytes(int nb, int ib, int G) {
     const int W = kThreads / G;
-    return ldc_of(nb, G) * W * 8 + lp_ldv(nb) * ib * 4 + ib * ib * 4 + 2 * ib * W * 4 + (ib + 1) * W * 8;
+    return 4 * (2 * lp2_ldc(nb) * W + 2 * lp2_ldv(nb) * ib + 2 * ib * ib + 2 * ib * (W + 8));
 }
 
 template <int G>
-__device__ __forceinline__ LpSmem lp_layout(const ExecParams& P, double* base) {
+__device__ __forceinline__ Lp2 lp2_layout(int nb, int ib, double* base) {
     constexpr int W = kThreads / G;
-    LpSmem s;
-    s.ldc = ldc_of(P.nb, G);
-    s.ldv = lp_ldv(P.nb);
-    s.ldt = P.ib + 1;
-    s.Cs = base;
-    s.Ct = s.Cs + s.ldc * W;
-    s.Vf = reinterpret_cast<float*>(s.Ct + s.ldt * W);
-    s.Tf = s.Vf + s.ldv * P.ib;
-    s.Wm = s.Tf + P.ib * P.ib;
-    s.W2 = s.Wm + P.ib * W;
-    return s;
+    Lp2 L;
+    L.ldc = lp2_ldc(nb);
+    L.ldv = lp2_ldv(nb);
+    L.ldw = W + 8;
+    float* f = reinterpret_cast<float*>(base);
+    L.Cf = f;
+    L.Ctf = L.Cf + L.ldc * W;
+    L.Vb[0] = L.Ctf + L.ldc * W;
+    L.Vb[1] = L.Vb[0] + L.ldv * ib;
+    L.Tb[0] = L.Vb[1] + L.ldv * ib;
+    L.Tb[1] = L.Tb[0] + ib * ib;
+    L.Wm = L.Tb[1] + ib * ib;
+    L.W2 = L.Wm + ib * L.ldw;
+    return L;
 }
 
-// One block of ib reflectors, staged in S.Vf (FP32, unit/zero structure
-// written out) with its T in S.Tf, applied to the strip in S.Cs (rows
-// [rlo, rhi)) and, for TT/TS, to the top rows in S.Ct:
-//   W = V^T C (+ C_top),  W2 = T^T W,  C_top -= W2,  C -= V W2.
+// Rows [r0, r1) of a strip of a column-major FP64 view <-> FP32 shared memory.
+__device__ __forceinline__ void strip_to_f32(float* dst, int ldd, const View& v, int r0, int r1, int c0, int W) {
+    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+        const bool rok = r < v.rv;
+#pragma unroll 8
+        for (int c = 0; c < W; ++c) {
+            double x = 0.0;
+            if (rok && c0 + c < v.cv) x = __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld);
+            dst[r + c * ldd] = static_cast<float>(x);
+        }
+    }
+}
+__device__ __forceinline__ void strip_from_f32(const float* src, int lds, const View& v, int r0, int r1, int c0,
+                                               int W) {
+    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+        if (r >= v.rv) continue;
+#pragma unroll 8
+        for (int c = 0; c < W; ++c)
+            if (c0 + c < v.cv) v.p[r + static_cast<int64_t>(c0 + c) * v.ld] = static_cast<double>(src[r + c * lds]);
+    }
+}
+
+// One block of ib reflectors (FP32 V_b in Vb, T_b in Tb) applied to the FP32
+// strip L.Cf (rows [rlo, rhi)) and, for TT/TS, to rows j0.. of L.Ctf:
+//   W = V_b^T C (+ C_top rows),  W2 = T_b^T W,  C_top rows -= W2,  C -= V_b W2.
+// Both products run on the tensor cores (m16n8k8 TF32, FP32 accumulation).
 template <int G, int MODE, int PREC>
-__device__ void lp_apply(const LpSmem& S, int ib, int rlo, int rhi) {
-    constexpr int W = kThreads / G;        // strip width (multiple of 8)
-    constexpr int NNT = W / 8;              // n-tiles of the strip
+__device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib, int j0, int rlo, int rhi) {
+    constexpr int W = kThreads / G;
+    constexpr int NNT = W / 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane >> 2, tig = lane & 3;
-    const int nmt1 = ib / 16;               // m-tiles of W (reflectors)
-    // W = V_b^T C over rows [rlo, rhi): warp w owns m-tile w % nmt1 and the
-    // n-tiles (w / nmt1) + (8 / nmt1) * t.
-    {
-        const int mt = warp % nmt1;
-        const int m0 = mt * 16;
-        constexpr int kMaxAcc = 8;
-        float acc[kMaxAcc][4];
-        const int nstep = 8 / nmt1;
-        int nts = 0;
-        for (int nt = warp / nmt1; nt < NNT; nt += nstep) ++nts;
+    const int nmt1 = ib / 16;
+        // W = V_b^T C: warp w owns m-tile w % nmt1 and n-tiles (w / nmt1) + (8 / nmt1) t.
+        {
+            const int m0 = (warp % nmt1) * 16;
+            constexpr int kMaxAcc = 8;
+            float acc[kMaxAcc][4];
+            const int nstep = 8 / nmt1;
 #pragma unroll
-        for (int a = 0; a < kMaxAcc; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
-        for (int k0 = rlo; k0 < rhi; k0 += 8) {
-            uint32_t ahi[4], alo[4];
-            split<PREC>(S.Vf[(k0 + tig) + (m0 + gid) * S.ldv], ahi[0], alo[0]);
-            split<PREC>(S.Vf[(k0 + tig) + (m0 + gid + 8) * S.ldv], ahi[1], alo[1]);
-            split<PREC>(S.Vf[(k0 + tig + 4) + (m0 + gid) * S.ldv], ahi[2], alo[2]);
-            split<PREC>(S.Vf[(k0 + tig + 4) + (m0 + gid + 8) * S.ldv], ahi[3], alo[3]);
+            for (int a = 0; a < kMaxAcc; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
+            for (int k0 = rlo; k0 < rhi; k0 += 8) {
+                uint32_t ahi[4], alo[4];
+                split_t<PREC>(Vb[(k0 + tig) + (m0 + gid) * L.ldv], ahi[0], alo[0]);
+                split_t<PREC>(Vb[(k0 + tig) + (m0 + gid + 8) * L.ldv], ahi[1], alo[1]);
+                split_t<PREC>(Vb[(k0 + tig + 4) + (m0 + gid) * L.ldv], ahi[2], alo[2]);
+                split_t<PREC>(Vb[(k0 + tig + 4) + (m0 + gid + 8) * L.ldv], ahi[3], alo[3]);
+#pragma unroll
+                for (int a = 0; a < kMaxAcc; ++a) {
+                    const int nt = warp / nmt1 + a * nstep;
+                    if (a * nstep < NNT && nt < NNT) {
+                        const int n0 = nt * 8;
+                        uint32_t bh0, bl0, bh1, bl1;
+                        split_t<PREC>(L.Cf[(k0 + tig) + (n0 + gid) * L.ldc], bh0, bl0);
+                        split_t<PREC>(L.Cf[(k0 + tig + 4) + (n0 + gid) * L.ldc], bh1, bl1);
+                        mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
+                    }
+                }
+            }
 #pragma unroll
             for (int a = 0; a < kMaxAcc; ++a) {
-                if (a < nts) {
-                    const int n0 = (warp / nmt1 + a * nstep) * 8;
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split<PREC>(static_cast<float>(S.Cs[(k0 + tig) + (n0 + gid) * S.ldc]), bh0, bl0);
-                    split<PREC>(static_cast<float>(S.Cs[(k0 + tig + 4) + (n0 + gid) * S.ldc]), bh1, bl1);
-                    mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
+                const int nt = warp / nmt1 + a * nstep;
+                if (a * nstep < NNT && nt < NNT) {
+                    const int n0 = nt * 8;
+                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig] = acc[a][0];
+                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig + 1] = acc[a][1];
+                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig] = acc[a][2];
+                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig + 1] = acc[a][3];
                 }
             }
         }
-#pragma unroll
-        for (int a = 0; a < kMaxAcc; ++a) {
-            if (a < nts) {
-                const int n0 = (warp / nmt1 + a * nstep) * 8;
-                S.Wm[(m0 + gid) * W + n0 + 2 * tig] = acc[a][0];
-                S.Wm[(m0 + gid) * W + n0 + 2 * tig + 1] = acc[a][1];
-                S.Wm[(m0 + gid + 8) * W + n0 + 2 * tig] = acc[a][2];
-                S.Wm[(m0 + gid + 8) * W + n0 + 2 * tig + 1] = acc[a][3];
-            }
-        }
-    }
-    __syncthreads();
-    // W2 = T^T (W + C_top); C_top -= W2.
-    for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
-        const int a = idx / W, n = idx % W;
-        float s = 0.0f;
-        for (int x = 0; x <= a; ++x) {
-            float w = S.Wm[x * W + n];
-            if (MODE != GE) w += static_cast<float>(S.Ct[x + n * S.ldt]);
-            s = fmaf(S.Tf[x + a * ib], w, s);
-        }
-        S.W2[a * W + n] = s;
-    }
-    __syncthreads();
-    if (MODE != GE)
+        __syncthreads();
+        // W2 = T^T (W + C_top rows)
         for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
             const int a = idx / W, n = idx % W;
-            S.Ct[a + n * S.ldt] -= static_cast<double>(S.W2[a * W + n]);
-        }
-    // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...
-    for (int mt = (rlo / 16) + warp; mt < rhi / 16; mt += 8) {
-        const int r0 = mt * 16;
-        for (int nt = 0; nt < NNT; ++nt) {
-            const int n0 = nt * 8;
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int k0 = 0; k0 < ib; k0 += 8) {
-                uint32_t ahi[4], alo[4];
-                split<PREC>(S.Vf[(r0 + gid) + (k0 + tig) * S.ldv], ahi[0], alo[0]);
-                split<PREC>(S.Vf[(r0 + gid + 8) + (k0 + tig) * S.ldv], ahi[1], alo[1]);
-                split<PREC>(S.Vf[(r0 + gid) + (k0 + tig + 4) * S.ldv], ahi[2], alo[2]);
-                split<PREC>(S.Vf[(r0 + gid + 8) + (k0 + tig + 4) * S.ldv], ahi[3], alo[3]);
-                uint32_t bh0, bl0, bh1, bl1;
-                split<PREC>(S.W2[(k0 + tig) * W + n0 + gid], bh0, bl0);
-                split<PREC>(S.W2[(k0 + tig + 4) * W + n0 + gid], bh1, bl1);
-                mma3<PREC>(acc, ahi, alo, bh0, bh1, bl0, bl1);
+            float sum = 0.0f;
+            for (int x = 0; x <= a; ++x) {
+                float w = L.Wm[x * L.ldw + n];
+                if (MODE != GE) w += L.Ctf[(j0 + x) + n * L.ldc];
+                sum = fmaf(Tb[x + a * ib], w, sum);
             }
-            S.Cs[(r0 + gid) + (n0 + 2 * tig) * S.ldc] -= static_cast<double>(acc[0]);
-            S.Cs[(r0 + gid) + (n0 + 2 * tig + 1) * S.ldc] -= static_cast<double>(acc[1]);
-            S.Cs[(r0 + gid + 8) + (n0 + 2 * tig) * S.ldc] -= static_cast<double>(acc[2]);
-            S.Cs[(r0 + gid + 8) + (n0 + 2 * tig + 1) * S.ldc] -= static_cast<double>(acc[3]);
+            L.W2[a * L.ldw + n] = sum;
         }
-    }
+        __syncthreads();
+        if (MODE != GE)
+            for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
+                const int a = idx / W, n = idx % W;
+                L.Ctf[(j0 + a) + n * L.ldc] -= L.W2[a * L.ldw + n];
+            }
+        // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...
+        for (int mt = (rlo / 16) + warp; mt < rhi / 16; mt += 8) {
+            const int r0 = mt * 16;
+            for (int nt = 0; nt < NNT; ++nt) {
+                const int n0 = nt * 8;
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                for (int k0 = 0; k0 < ib; k0 += 8) {
+                    uint32_t ahi[4], alo[4];
+                    split_t<PREC>(Vb[(r0 + gid) + (k0 + tig) * L.ldv], ahi[0], alo[0]);
+                    split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig) * L.ldv], ahi[1], alo[1]);
+                    split_t<PREC>(Vb[(r0 + gid) + (k0 + tig + 4) * L.ldv], ahi[2], alo[2]);
+                    split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig + 4) * L.ldv], ahi[3], alo[3]);
+                    uint32_t bh0, bl0, bh1, bl1;
+                    split_t<PREC>(L.W2[(k0 + tig) * L.ldw + n0 + gid], bh0, bl0);
+                    split_t<PREC>(L.W2[(k0 + tig + 4) * L.ldw + n0 + gid], bh1, bl1);
+                    mma3<PREC>(acc, ahi, alo, bh0, bh1, bl0, bl1);
+                }
+                L.Cf[(r0 + gid) + (n0 + 2 * tig) * L.ldc] -= acc[0];
+                L.Cf[(r0 + gid) + (n0 + 2 * tig + 1) * L.ldc] -= acc[1];
+                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig) * L.ldc] -= acc[2];
+                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig + 1) * L.ldc] -= acc[3];
+            }
+        }
 }
 
+// Update task in low precision: C (and C_top) converted to FP32 once, every
+// block of ib reflectors applied with two tensor-core products,
+//   W = V_b^T C (+ C_top rows),  W2 = T_b^T W,  C_top rows -= W2,  C -= V_b W2,
+// then converted back.  Reflector blocks and T arrive in FP32 from the panel
+// task (unit/zero structure written out) by double-buffered cp.async.
 template <int G, int MODE, int PREC>
 __device__ void update_task_lp(const ExecParams& P, const DevTask& T, double* smem) {
     constexpr int W = kThreads / G;
-    const LpSmem S = lp_layout<G>(P, smem);
     const int nb = P.nb, ib = P.ib;
-    const View vt = tile_view(P, T.i, T.k);
-    const int64_t toff = (static_cast<int64_t>(T.k) * P.p + T.i);
-    const double* Tsrc = ((MODE == GE) ? P.T_ge : P.T_el) + toff * ib * nb;
+    const Lp2 L = lp2_layout<G>(nb, ib, smem);
+    const int64_t tile = static_cast<int64_t>(T.k) * P.p + T.i;
+    const float* Vt = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
+    const float* Tt = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
     const int c0 = T.strip * W;
     const View bot = tile_view(P, T.i, T.j);
     const View top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
-    load_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W);
-    for (int j0 = 0; j0 < nb; j0 += ib) {
-        // Rows of C touched by this block's reflectors.
+    const int nblk = nb / ib;
+
+    auto stage = [&](int b, int buf) {
+        const int j0 = b * ib;
         const int rlo = (MODE == GE) ? j0 : 0;
         const int rhi = (MODE == TT) ? j0 + ib : nb;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < (rhi - rlo) * ib; idx += kThreads) {
-            const int r = rlo + idx % (rhi - rlo);
-            const int jj = idx / (rhi - rlo);
-            const int j = j0 + jj;
-            float v = 0.0f;
-            if (MODE == GE) {
-                if (r == j) v = 1.0f;
-                else if (r > j && r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
-            } else if (MODE == TT) {
-                if (r <= j && r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
-            } else {
-                if (r < vt.rv && j < vt.cv) v = static_cast<float>(__ldcg(vt.p + r + static_cast<int64_t>(j) * vt.ld));
-            }
-            S.Vf[r + jj * S.ldv] = v;
+        const int chunks = (rhi - rlo) / 4;
+        for (int idx = threadIdx.x; idx < chunks * ib; idx += kThreads) {
+            const int jj = idx / chunks, c = idx % chunks;
+            cp_async16(L.Vb[buf] + rlo + 4 * c + jj * L.ldv, Vt + rlo + 4 * c + static_cast<int64_t>(j0 + jj) * nb);
         }
-        for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads)
-            S.Tf[idx] = static_cast<float>(__ldcg(Tsrc + static_cast<int64_t>(j0) * ib + idx));
-        if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-        __syncthreads();
-        lp_apply<G, MODE, PREC>(S, ib, rlo, rhi);
-        if (MODE != GE) {
-            __syncthreads();
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+        for (int idx = threadIdx.x; idx < ib * ib / 4; idx += kThreads)
+            cp_async16(L.Tb[buf] + 4 * idx, Tt + static_cast<int64_t>(j0) * ib + 4 * idx);
+        cp_commit();
+    };
+
+    stage(0, 0);
+    strip_to_f32(L.Cf, L.ldc, bot, 0, nb, c0, W);
+    if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, 0, nb, c0, W);
+    for (int b = 0; b < nblk; ++b) {
+        const int buf = b & 1;
+        const int j0 = b * ib;
+        const int rlo = (MODE == GE) ? j0 : 0;
+        const int rhi = (MODE == TT) ? j0 + ib : nb;
+        if (b + 1 < nblk) {
+            stage(b + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
+        __syncthreads();
+        lp2_block<G, MODE, PREC>(L, L.Vb[buf], L.Tb[buf], ib, j0, rlo, rhi);
+        __syncthreads();
     }
-    __syncthreads();
-    store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
+    strip_from_f32(L.Cf, L.ldc, bot, 0, nb, c0, W);
+    if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, 0, nb, c0, W);
 }
 
-// Shared memory of a panel task's low-precision trailing update: Vf overlays
-// the FP64 reflector block (converted after it was written back); Tf, Wm, W2
-// follow Vf when they fit in that region, else they follow tau.
-__host__ __device__ inline bool panel_lp_fits(int nb, int ib, int G) {
-    const int W = kThreads / G;
-    return (lp_ldv(nb) * ib + ib * ib + 2 * ib * W) * 4 <= nb * ib * 8;
-}
-
-__host__ __device__ inline int panel_lp_extra_bytes(int nb, int ib, int G) {
-    const int W = kThreads / G;
-    return panel_lp_fits(nb, ib, G) ? 0 : (ib * ib + 2 * ib * W) * 4;
-}
-
-// After a panel block is factored (Vs, taus) and its T is in Tb64 (FP64,
-// ib x ib, in the strip area): the trailing columns [j0+ib, ncol) of the tile
-// pair get the block on the tensor cores.
+// Trailing update of a panel task in low precision: block j0's FP32 V and T
+// (just written to the handle) come back by cp.async; the trailing columns
+// [j0+ib, ncol) of the tile pair are converted to FP32 strip by strip and
+// updated on the tensor cores.  The whole shared memory is free here.
 template <int G, int MODE, int PREC>
-__device__ void panel_lp_trailing(const Smem& S, const View& top, const View& bot, int nb, int ib, int j0,
-                                  int ncol, const double* Tb64) {
+__device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
+                                  int ncol, double* smem) {
     constexpr int W = kThreads / G;
-    constexpr int kMaxReg = 64;             // nb * ib <= 256 * 64 values over 256 threads
-    LpSmem L;
-    L.Cs = S.Cs;
-    L.ldc = S.ldc;
-    L.Ct = S.Ct;
-    L.ldt = S.ldt;
-    L.ldv = lp_ldv(nb);
-    L.Vf = reinterpret_cast<float*>(S.Vs);
-    if (panel_lp_fits(nb, ib, G)) L.Tf = L.Vf + L.ldv * ib;
-    else L.Tf = reinterpret_cast<float*>(S.taus + ib);
-    L.Wm = L.Tf + ib * ib;
-    L.W2 = L.Wm + ib * W;
+    const int nb = P.nb, ib = P.ib;
+    const Lp2 L = lp2_layout<G>(nb, ib, smem);
+    const int64_t tile = static_cast<int64_t>(k) * P.p + i;
+    const float* Vt = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
+    const float* Tt = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
     const int rlo = (MODE == GE) ? j0 : 0;
     const int rhi = (MODE == TT) ? j0 + ib : nb;
-    const int nv = (rhi - rlo) * ib;
-    // Vs (FP64) -> registers -> Vf (FP32) in place; T (FP64) -> registers.
-    float buf[kMaxReg];
-    float tb[kMaxReg / 4 + 1];
-#pragma unroll
-    for (int e = 0; e < kMaxReg; ++e) {
-        const int idx = threadIdx.x + e * kThreads;
-        float v = 0.0f;
-        if (idx < nv) {
-            const int r = rlo + idx % (rhi - rlo);
-            const int jj = idx / (rhi - rlo);
-            const int j = j0 + jj;
-            const double x = S.Vs[r + jj * nb];
-            if (MODE == GE) v = (r == j) ? 1.0f : (r > j ? static_cast<float>(x) : 0.0f);
-            else if (MODE == TT) v = (r <= j) ? static_cast<float>(x) : 0.0f;
-            else v = static_cast<float>(x);
-        }
-        buf[e] = v;
+    __syncthreads();                       // the block's V / T writes are done
+    const int chunks = (rhi - rlo) / 4;
+    for (int idx = threadIdx.x; idx < chunks * ib; idx += kThreads) {
+        const int jj = idx / chunks, c = idx % chunks;
+        cp_async16(L.Vb[0] + rlo + 4 * c + jj * L.ldv, Vt + rlo + 4 * c + static_cast<int64_t>(j0 + jj) * nb);
     }
-#pragma unroll
-    for (int e = 0; e < kMaxReg / 4 + 1; ++e) {
-        const int idx = threadIdx.x + e * kThreads;
-        tb[e] = (idx < ib * ib) ? static_cast<float>(Tb64[idx]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < kMaxReg; ++e) {
-        const int idx = threadIdx.x + e * kThreads;
-        if (idx < nv) {
-            const int r = rlo + idx % (rhi - rlo);
-            const int jj = idx / (rhi - rlo);
-            L.Vf[r + jj * L.ldv] = buf[e];
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < kMaxReg / 4 + 1; ++e) {
-        const int idx = threadIdx.x + e * kThreads;
-        if (idx < ib * ib) L.Tf[idx] = tb[e];
-    }
+    for (int idx = threadIdx.x; idx < ib * ib / 4; idx += kThreads)
+        cp_async16(L.Tb[0] + 4 * idx, Tt + static_cast<int64_t>(j0) * ib + 4 * idx);
+    cp_commit();
+    cp_wait<0>();
     for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
         __syncthreads();
-        if (MODE == GE) {
-            load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
-        } else {
-            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-            load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
-        }
+        strip_to_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
+        if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
         __syncthreads();
-        lp_apply<G, MODE, PREC>(L, ib, rlo, rhi);
+        lp2_block<G, MODE, PREC>(L, L.Vb[0], L.Tb[0], ib, j0, rlo, rhi);
         __syncthreads();
-        if (MODE == GE) {
-            store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
-        } else {
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
-            store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
-        }
+        strip_from_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
+        if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
     }
 }
 
@@ -908,14 +900,14 @@ __global__ void form_t_kernel(ExecParams P, const int32_t* panels, double* T_ge,
 int strip_width(int G) { return kThreads / G; }
 
 int lp_smem_bytes(int nb, int ib, int G) {
-    const int panel = smem_doubles(nb, ib, G) * 8 + panel_lp_extra_bytes(nb, ib, G);
-    const int upd = lp_bytes(nb, ib, G);
+    const int panel = smem_doubles(nb, ib, G) * 8;
+    const int upd = lp2_bytes(nb, ib, G);
     return panel > upd ? panel : upd;
 }
 
 bool lp_supported(int nb, int ib, int G) {
     const int W = kThreads / G;
-    return nb % 16 == 0 && ib % 16 == 0 && 8 % (ib / 16) == 0 && W % 8 == 0 && W / 8 <= 8;
+    return nb % 16 == 0 && ib % 16 == 0 && ib <= 64 && 8 % (ib / 16) == 0 && W % 8 == 0 && W / 8 <= 8;
 }
 
 bool choose_layout(int nb, int ib, int* G, int* smem_bytes) {

@@ -95,8 +95,10 @@ struct ExecParams {
     double* B; int64_t ldb, nrhs;                // right-hand side (apply graphs), else null
     int trans;                                   // 1: apply Q^T, 0: apply Q
     int prec;                                    // 0: FP64 updates, 1: split-TF32 (3 pass), 2: TF32
-    double* T_ge;                                // compact-WY T blocks (prec != 0): ib x nb per tile
-    double* T_el;
+    float* T_ge;                                 // compact-WY T blocks (prec != 0), FP32: ib x nb per tile
+    float* T_el;
+    float* V_ge;                                 // reflectors as FP32 with unit/zero structure written
+    float* V_el;                                 //   out (prec != 0): nb x nb per tile, column-major
     const DevTask* tasks; const int32_t* succ_ptr; const int32_t* succ;
     int32_t* deps; int32_t* queue; uint32_t* ctr; int32_t* status;
     int32_t ntasks;
