@@ -214,6 +214,40 @@ int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b, double* x,
               tqr_lstsq_info* info);
 
 /* ---------------------------------------------------------------------------
+ * Batched factorization: `count` independent matrices in one persistent
+ * launch.  The task graphs of all matrices are concatenated; any CTA may run
+ * any matrix's ready task, so small matrices fill the GPU together.
+ *   A:  host array of `count` device pointers, matrix c is m[c] x n[c],
+ *       column-major with leading dimension m[c], overwritten by R and V.
+ *   nb, ib, tree, BS: host arrays of per-matrix parameters (as tqr_factor),
+ *       so every size class can use its own tuned configuration.
+ *   out: receives the batch handle.  If *out was made by a call with the same
+ *       count and identical A, m, n, nb, ib, tree and BS arrays, it is launched
+ *       again without any allocation or host-to-device copy (such a call can be
+ *       captured into a CUDA graph); otherwise a new handle is built (allocates
+ *       and copies; the old one is left untouched).
+ * Argument errors: -1 count, -2 A, -3 m, -4 n, -5 nb, -6 ib, -7 tree, -8 BS,
+ * -10 out, each for the first offending matrix. */
+typedef struct tqr_batch tqr_batch;
+
+typedef struct {
+    int32_t count;          /* matrices                                    */
+    int32_t strip;          /* columns per update task                      */
+    int64_t n_tasks;        /* device tasks of the combined graph           */
+    int64_t n_edges;        /* dependency edges                             */
+    int64_t max_critical_path; /* largest unit-weight critical path         */
+    double flops;           /* sum of 2 n^2 (m - n/3)                       */
+} tqr_batch_info;
+
+int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
+                       const int32_t* ib, const int32_t* tree, const int32_t* BS, void* stream,
+                       tqr_batch** out);
+/* Waits for the batch's last launch; returns its device status. */
+int tqr_batch_sync(tqr_batch* b);
+int tqr_batch_get_info(const tqr_batch* b, tqr_batch_info* info);
+void tqr_batch_free(tqr_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Host-only integer entry points (no GPU needed).
  * ------------------------------------------------------------------------- */
 

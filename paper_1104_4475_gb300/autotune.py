@@ -1,0 +1,125 @@
+"""Autotuner for batched tall-skinny factorizations.
+
+For each size class -- a column count n and a range of row counts m -- every
+candidate (nb, ib, tree, BS) is timed on a sample batch of that class (one
+batched launch per candidate, CUDA events, best of ``reps`` after a warm-up)
+and the fastest is kept.  Results form a versioned JSON database that can be
+saved and reloaded; :func:`lookup` maps any (m, n) to its class's choice.
+
+The search is exhaustive over the candidate set; a learned cost model can
+replace it by ranking candidates without timing them (see ``costmodel``).
+"""
+
+import json
+import os
+
+import numpy as np
+
+from . import tqr
+
+DB_VERSION = 1
+M_BUCKETS = [(512, 1024), (1024, 2048), (2048, 4096), (4096, 8192), (8192, 16385)]
+N_CLASSES = [32, 64, 128]
+TREE_CANDIDATES = [(tqr.GREEDY, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1), (tqr.FLAT_TT, 1), (tqr.FLAT_TS, 1),
+                   (tqr.PLASMA, 4), (tqr.PLASMA, 16), (tqr.ASAP, 1)]
+
+
+def candidates(n, m_lo):
+    """(nb, ib, tree, BS) candidates for matrices with n columns."""
+    out = []
+    for nb in (16, 32, 64, 128):
+        if nb > n or nb > m_lo:
+            continue
+        for ib in (8, 16, 32):
+            if ib > nb or nb % ib:
+                continue
+            for tree, BS in TREE_CANDIDATES:
+                p_min = -(-m_lo // nb)
+                out.append((nb, ib, tree, min(BS, p_min)))
+    return out
+
+
+def sample_class(n, m_lo, m_hi, count, seed):
+    rng = np.random.default_rng(seed)
+    return [int(m) for m in rng.integers(m_lo, m_hi, count)]
+
+
+def time_batch(ms, n, cfg, reps=2, seed=0):
+    """Seconds for one batched launch of matrices (ms[i] x n) with config cfg."""
+    import torch
+    nb, ib, tree, BS = cfg
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    src = [torch.randn(n, m, generator=g, dtype=torch.float64, device="cuda").t() for m in ms]
+    work = [torch.empty_like(s.t()).t() for s in src]
+    b = None
+    best = None
+    for r in range(reps + 1):
+        for w, s in zip(work, src):
+            w.copy_(s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b = tqr.tqr_factor_batched(work, nb, ib, tree, BS, reuse=b)
+        e1.record()
+        tqr.tqr_batch_sync(b)
+        t = e0.elapsed_time(e1) / 1e3
+        if r > 0:
+            best = t if best is None else min(best, t)
+    b.free()
+    return best
+
+
+def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, log=None):
+    """Exhaustive search; returns the database (a dict)."""
+    import torch
+    classes = []
+    for n in n_classes:
+        for (lo, hi) in m_buckets:
+            ms = sample_class(n, lo, hi, sample, seed + n + lo)
+            results = []
+            for cfg in candidates(n, lo):
+                try:
+                    t = time_batch(ms, n, cfg, reps=reps, seed=seed)
+                except tqr.TqrError:
+                    continue
+                results.append((t, cfg))
+            results.sort()
+            t, (nb, ib, tree, BS) = results[0]
+            flops = sum(2.0 * n * n * (m - n / 3.0) for m in ms)
+            rec = {"n": n, "m_lo": lo, "m_hi": hi, "nb": nb, "ib": ib, "tree": tree, "BS": BS, "seconds": t,
+                   "gflops": flops / t / 1e9, "candidates": len(results),
+                   "worst_seconds": results[-1][0]}
+            classes.append(rec)
+            if log:
+                log(rec)
+    return {"version": DB_VERSION, "gpu": torch.cuda.get_device_name(0), "sample": sample, "classes": classes}
+
+
+def save(db, path):
+    with open(path, "w") as fh:
+        json.dump(db, fh, indent=1)
+
+
+def load(path):
+    with open(path) as fh:
+        db = json.load(fh)
+    if db.get("version") != DB_VERSION:
+        raise ValueError("autotune database version %r, expected %d" % (db.get("version"), DB_VERSION))
+    return db
+
+
+def lookup(db, m, n):
+    """The tuned (nb, ib, tree, BS) for an m x n matrix: its class, or the
+    nearest class in n and m."""
+    best, key = None, None
+    for c in db["classes"]:
+        dn = abs(np.log2(n) - np.log2(c["n"]))
+        dm = 0.0 if c["m_lo"] <= m < c["m_hi"] else min(abs(np.log2(m / c["m_lo"])), abs(np.log2(m / c["m_hi"])))
+        d = (dn, dm)
+        if best is None or d < key:
+            best, key = c, d
+    nb = min(best["nb"], n)
+    ib = min(best["ib"], nb)
+    BS = best["BS"]
+    if best["tree"] == tqr.PLASMA:
+        BS = max(1, min(BS, -(-m // nb)))
+    return nb, ib, best["tree"], BS

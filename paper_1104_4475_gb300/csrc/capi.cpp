@@ -189,9 +189,83 @@ static cudaError_t alloc_state(ExecState& s, int32_t cap, int32_t* status) {
     return cudaSuccess;
 }
 
+// Host-side plan of one matrix of a batch: its factor graph for strips of W.
+struct HostPlan {
+    int p = 0, q = 0;
+    int64_t cp = 0;
+    Graph g;
+};
+
+static std::mutex g_hplans_mu;
+static std::map<std::tuple<int64_t, int64_t, int, int, int, int, int>, std::shared_ptr<HostPlan>>& hplans() {
+    static auto* m = new std::map<std::tuple<int64_t, int64_t, int, int, int, int, int>, std::shared_ptr<HostPlan>>();
+    return *m;
+}
+
+static int host_plan(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int W, std::shared_ptr<HostPlan>& out) {
+    const auto key = std::make_tuple(m, n, nb, ib, tree, BS, W);
+    {
+        std::lock_guard<std::mutex> lk(g_hplans_mu);
+        auto it = hplans().find(key);
+        if (it != hplans().end()) {
+            out = it->second;
+            return TQR_OK;
+        }
+    }
+    auto H = std::make_shared<HostPlan>();
+    H->p = static_cast<int>((m + nb - 1) / nb);
+    H->q = static_cast<int>((n + nb - 1) / nb);
+    std::vector<Elim> el;
+    int rc = make_elims(H->p, H->q, tree, BS, el);
+    if (rc != TQR_OK) return rc;
+    std::vector<TileTask> tt;
+    expand_tasks(H->p, H->q, el, tree == TQR_FLAT_TS, tt);
+    H->cp = simulate(H->p, H->q, tt, nullptr);
+    build_factor_graph(H->p, H->q, nb, W, static_cast<int>(n - static_cast<int64_t>(H->q - 1) * nb), tt, H->g);
+    std::lock_guard<std::mutex> lk(g_hplans_mu);
+    hplans()[key] = H;
+    out = H;
+    return TQR_OK;
+}
+
 }  // namespace tqr
 
 using namespace tqr;
+
+struct tqr_batch {
+    int count = 0;
+    std::vector<double*> A;
+    std::vector<int64_t> m, n;
+    std::vector<int32_t> nb, ib, tree, BS;
+    DevGraphOwner dg;
+    MatDesc* d_mats = nullptr;
+    double* tau_ge = nullptr;
+    double* tau_el = nullptr;
+    int32_t* status = nullptr;
+    ExecState st;
+    int G = 4, smem = 0;
+    int64_t max_cp = 0;
+    double flops = 0.0;
+    cudaStream_t stream = nullptr;
+    ~tqr_batch() {
+        cudaFree(d_mats);
+        cudaFree(tau_ge);
+        cudaFree(tau_el);
+        cudaFree(status);
+        cudaFree(st.deps);
+        cudaFree(st.queue);
+        cudaFree(st.ctr);
+    }
+    bool same(int c, double* const* a, const int64_t* mm, const int64_t* nn, const int32_t* b, const int32_t* ii,
+              const int32_t* tr, const int32_t* bs) const {
+        if (c != count) return false;
+        for (int x = 0; x < c; ++x)
+            if (A[x] != a[x] || m[x] != mm[x] || n[x] != nn[x] || nb[x] != b[x] || ib[x] != ii[x] ||
+                tree[x] != tr[x] || BS[x] != bs[x])
+                return false;
+        return true;
+    }
+};
 
 struct tqr_factors {
     std::shared_ptr<Plan> plan;
@@ -258,6 +332,7 @@ static ExecParams base_params(const tqr_factors* f) {
     x.V_ge = f->V_ge;
     x.V_el = f->V_el;
     x.trace = nullptr;
+    x.mats = nullptr;
     x.timeout_ns = timeout_ns(lapack_flops(P.key.m, P.key.n));
     return x;
 }
@@ -487,7 +562,7 @@ int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count) {
         for (int64_t t = 0; t < nt; ++t) {
             const DevTask& x = P.g.tasks[t];
             int64_t* o = out + 8 * t;
-            o[0] = x.kind;
+            o[0] = x.kind & 0xff;
             o[1] = x.i;
             o[2] = x.piv;
             o[3] = x.k;
@@ -698,6 +773,134 @@ int tqr_inject_fault(int kind) {
     if (kind != 0 && kind != 1) return -1;
     g_fault = kind;
     return TQR_OK;
+}
+
+static int launch_batch(tqr_batch* b) {
+    ExecParams P{};
+    P.tau_ge = b->tau_ge;
+    P.tau_el = b->tau_el;
+    P.trans = 1;
+    P.mats = b->d_mats;
+    P.timeout_ns = timeout_ns(b->flops);
+    P.nb = b->nb.empty() ? 0 : b->nb[0];
+    P.ib = b->ib.empty() ? 0 : b->ib[0];
+    const cudaError_t e = launch_factor_exec(P, b->dg.d, b->st, b->G, b->smem, true, b->stream);
+    return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
+                       const int32_t* ib, const int32_t* tree, const int32_t* BS, void* stream,
+                       tqr_batch** out) {
+    try {
+        if (count < 1 || count > (1 << 23)) return -1;
+        if (!A) return -2;
+        if (!m) return -3;
+        if (!n) return -4;
+        if (!nb) return -5;
+        if (!ib) return -6;
+        if (!tree) return -7;
+        if (!BS) return -8;
+        if (!out) return -10;
+        int nbmax = 0, ibmax = 0;
+        for (int c = 0; c < count; ++c) {
+            const int rc = check_common(A[c], m[c], n[c], nb[c], ib[c]);
+            if (rc != TQR_OK) return rc == -1 ? -2 : (rc == -2 ? -3 : (rc == -3 ? -4 : (rc == -4 ? -5 : -6)));
+            if (tree[c] < TQR_FLAT_TS || tree[c] > TQR_GRASAP) return -7;
+            const int p = static_cast<int>((m[c] + nb[c] - 1) / nb[c]);
+            const int q = static_cast<int>((n[c] + nb[c] - 1) / nb[c]);
+            if (tree[c] == TQR_PLASMA && (BS[c] < 1 || BS[c] > p)) return -8;
+            if (tree[c] == TQR_GRASAP && (BS[c] < 0 || BS[c] > q)) return -8;
+            nbmax = std::max(nbmax, nb[c]);
+            ibmax = std::max(ibmax, ib[c]);
+        }
+        tqr_batch* b = *out;
+        if (b && b->same(count, A, m, n, nb, ib, tree, BS)) {
+            b->stream = static_cast<cudaStream_t>(stream);
+            return launch_batch(b);
+        }
+        auto nbh = std::make_unique<tqr_batch>();
+        b = nbh.get();
+        b->count = count;
+        b->A.assign(A, A + count);
+        b->m.assign(m, m + count);
+        b->n.assign(n, n + count);
+        b->nb.assign(nb, nb + count);
+        b->ib.assign(ib, ib + count);
+        b->tree.assign(tree, tree + count);
+        b->BS.assign(BS, BS + count);
+        if (!choose_layout(nbmax, ibmax, &b->G, &b->smem)) return TQR_ERR_UNSUPPORTED;
+        const int W = strip_width(b->G);
+        Graph all;
+        std::vector<MatDesc> mats(count);
+        int64_t tau_off = 0;
+        for (int c = 0; c < count; ++c) {
+            const int t = tree[c] == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree[c];
+            const int bs = (t == TQR_PLASMA || t == TQR_GRASAP) ? BS[c] : 0;
+            std::shared_ptr<HostPlan> H;
+            const int rc = host_plan(m[c], n[c], nb[c], ib[c], t, bs, W, H);
+            if (rc != TQR_OK) return rc;
+            b->smem = std::max(b->smem, fp64_smem_bytes(nb[c], ib[c], b->G));
+            b->max_cp = std::max(b->max_cp, H->cp);
+            b->flops += lapack_flops(m[c], n[c]);
+            const int32_t off = static_cast<int32_t>(all.tasks.size());
+            if (static_cast<int64_t>(off) + static_cast<int64_t>(H->g.tasks.size()) > 0x7fffffff) return TQR_ERR_UNSUPPORTED;
+            for (const DevTask& x : H->g.tasks) {
+                DevTask y = x;
+                y.kind = x.kind | (c << 8);
+                all.tasks.push_back(y);
+            }
+            const int32_t eoff = static_cast<int32_t>(all.succ.size());
+            if (all.succ_ptr.empty()) all.succ_ptr.push_back(0);
+            for (size_t t2 = 1; t2 < H->g.succ_ptr.size(); ++t2) all.succ_ptr.push_back(H->g.succ_ptr[t2] + eoff);
+            for (int32_t sx : H->g.succ) all.succ.push_back(sx + off);
+            all.indeg.insert(all.indeg.end(), H->g.indeg.begin(), H->g.indeg.end());
+            for (int32_t r : H->g.ready) all.ready.push_back(r + off);
+            mats[c] = MatDesc{A[c], m[c], m[c], n[c], nb[c], ib[c], H->p, H->q, tau_off};
+            tau_off += static_cast<int64_t>(H->p) * H->q * nb[c];
+        }
+        if (upload_graph(all, b->dg) != cudaSuccess) return TQR_ERR_NOMEM;
+        if (upload(&b->d_mats, mats) != cudaSuccess) return TQR_ERR_NOMEM;
+        if (cudaMalloc(&b->tau_ge, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess ||
+            alloc_state(b->st, b->dg.d.ntasks, b->status) != cudaSuccess)
+            return TQR_ERR_NOMEM;
+        b->stream = static_cast<cudaStream_t>(stream);
+        const int rc = launch_batch(b);
+        if (rc != TQR_OK) return rc;
+        *out = nbh.release();
+        return TQR_OK;
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_batch_sync(tqr_batch* b) {
+    if (!b) return -1;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TQR_ERR_CUDA;
+    int32_t st = 0;
+    if (cudaMemcpy(&st, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return TQR_ERR_CUDA;
+    return st;
+}
+
+int tqr_batch_get_info(const tqr_batch* b, tqr_batch_info* info) {
+    if (!b) return -1;
+    if (!info) return -2;
+    info->count = b->count;
+    info->strip = strip_width(b->G);
+    info->n_tasks = b->dg.d.ntasks;
+    info->n_edges = b->dg.d.nedges;
+    info->max_critical_path = b->max_cp;
+    info->flops = b->flops;
+    return TQR_OK;
+}
+
+void tqr_batch_free(tqr_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    delete b;
 }
 
 const char* tqr_strerror(int status) {

@@ -125,16 +125,27 @@ __device__ __forceinline__ View rhs_view(const ExecParams& P, int i, int c0) {
 }
 
 // dst[(r - rbase) + c*ldd] = src(r, c0 + c) for r in [r0, r1), c in [0, nc).
+// Each thread keeps eight loads in flight before storing them.
 __device__ __forceinline__ void load_rect(double* dst, int ldd, int rbase, const View& v, int r0,
                                           int r1, int c0, int nc) {
     const int nr = r1 - r0;
     if (nr <= 0) return;
-    for (int idx = threadIdx.x; idx < nr * nc; idx += kThreads) {
-        const int r = r0 + idx % nr;
-        const int c = idx / nr;
-        double x = 0.0;
-        if (r < v.rv && c0 + c < v.cv) x = __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld);
-        dst[(r - rbase) + c * ldd] = x;
+    const int total = nr * nc;
+    for (int base = threadIdx.x; base < total; base += 8 * kThreads) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads;
+            const int r = r0 + idx % nr;
+            const int c = idx / nr;
+            x[u] = (idx < total && r < v.rv && c0 + c < v.cv)
+                       ? __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads;
+            if (idx < total) dst[(r0 + idx % nr - rbase) + (idx / nr) * ldd] = x[u];
+        }
     }
 }
 
@@ -174,9 +185,10 @@ __device__ __forceinline__ double warp_sum(double x) {
 // hazards between threads, only the G-lane reductions.
 // ----------------------------------------------------------------------------
 template <int G, int MODE>
-__device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int ib, int trans) {
+__device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int ib, int trans, int ncols) {
     const int c = threadIdx.x / G;
     const int g = threadIdx.x % G;
+    if ((threadIdx.x / 32) * (32 / G) >= ncols) return;   // this warp's columns do not exist
     double* Cc = S.Cs + c * S.ldc;
     for (int s = 0; s < ib; ++s) {
         const int jj = trans ? s : ib - 1 - s;
@@ -343,7 +355,7 @@ __device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* s
                     load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
                 }
                 __syncthreads();
-                apply_block<G, MODE>(S, nb, j0, ib, 1);
+                apply_block<G, MODE>(S, nb, j0, ib, 1, ncol - c0);
                 __syncthreads();
                 if (MODE == GE) {
                     store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
@@ -389,7 +401,7 @@ __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem)
         for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
         if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
         __syncthreads();
-        apply_block<G, MODE>(S, nb, j0, ib, P.trans);
+        apply_block<G, MODE>(S, nb, j0, ib, P.trans, bot.cv - c0);
         if (MODE != GE) {
             __syncthreads();
             store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
@@ -735,7 +747,7 @@ __device__ __forceinline__ void update_any(const ExecParams& P, const DevTask& T
 
 template <int G, int PREC>
 __device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
-    switch (T.kind) {
+    switch (T.kind & 0xff) {
         case GEQRT: panel_task<G, GE, PREC>(P, T.i, -1, T.k, smem); break;
         case TTQRT: panel_task<G, TT, PREC>(P, T.i, T.piv, T.k, smem); break;
         case TSQRT: panel_task<G, TS, PREC>(P, T.i, T.piv, T.k, smem); break;
@@ -809,7 +821,23 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
         const DevTask T = P.tasks[t];
         uint64_t t_begin = 0;
         if (P.trace && threadIdx.x == 0) t_begin = globaltimer();
-        run_task<G, PREC>(P, T, smem);
+        if (P.mats) {
+            ExecParams Q = P;
+            const MatDesc d = P.mats[T.kind >> 8];
+            Q.A = d.A;
+            Q.lda = d.lda;
+            Q.m = d.m;
+            Q.n = d.n;
+            Q.nb = d.nb;
+            Q.ib = d.ib;
+            Q.p = d.p;
+            Q.q = d.q;
+            Q.tau_ge = P.tau_ge + d.tau_off;
+            Q.tau_el = P.tau_el + d.tau_off;
+            run_task<G, PREC>(Q, T, smem);
+        } else {
+            run_task<G, PREC>(P, T, smem);
+        }
         __syncthreads();
         if (P.trace && threadIdx.x == 0) {
             uint32_t sm;
@@ -898,6 +926,8 @@ __global__ void form_t_kernel(ExecParams P, const int32_t* panels, double* T_ge,
 // Host-side launch helpers.
 // ----------------------------------------------------------------------------
 int strip_width(int G) { return kThreads / G; }
+
+int fp64_smem_bytes(int nb, int ib, int G) { return smem_doubles(nb, ib, G) * static_cast<int>(sizeof(double)); }
 
 int lp_smem_bytes(int nb, int ib, int G) {
     const int panel = smem_doubles(nb, ib, G) * 8;

@@ -24,12 +24,20 @@ struct TileTask { int32_t kind, i, piv, k, j; };     // 0-based; piv/j = -1 when
 // One device task.  Update kernels are split into column strips: `strip`
 // selects columns [strip*W, strip*W + W) of tile column j (or of B).
 struct DevTask {
-    int32_t kind;    // Kind
+    int32_t kind;    // Kind in bits 0-7; matrix of a batched factorization in bits 8-31
     int32_t i;       // row of the tile factored / zeroed / updated
     int32_t piv;     // pivot row (TT/TS kernels), else -1
     int32_t k;       // panel column
     int32_t j;       // update column (updates), else -1
     int32_t strip;   // column strip (updates), else 0
+};
+
+// One matrix of a batched factorization (device array indexed by DevTask::kind >> 8).
+struct MatDesc {
+    double* A;
+    int64_t lda, m, n;
+    int32_t nb, ib, p, q;
+    int64_t tau_off;   // offset of this matrix's tau in tau_ge / tau_el
 };
 
 // ---- host planner (planner.cpp) ----
@@ -104,6 +112,7 @@ struct ExecParams {
     int32_t ntasks;
     uint64_t timeout_ns;                         // limit for any single wait
     uint64_t* trace;                             // optional: 2 per task (start, duration | sm << 56)
+    const MatDesc* mats;                         // batched factorization: per-matrix fields, else null
 };
 
 // Row groups per strip column (G) and dynamic shared memory for (nb, ib);
@@ -114,6 +123,7 @@ bool choose_layout(int nb, int ib, int* G, int* smem_bytes);
 int lp_smem_bytes(int nb, int ib, int G);
 bool lp_supported(int nb, int ib, int G);
 int strip_width(int G);
+int fp64_smem_bytes(int nb, int ib, int G);
 int device_sm_count();
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,
                                int smem, bool reset_status, cudaStream_t s);

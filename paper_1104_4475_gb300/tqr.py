@@ -47,6 +47,11 @@ class tqr_lstsq_info(ctypes.Structure):
                 ("solve_seconds", ctypes.c_double)]
 
 
+class tqr_batch_info(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("strip", ctypes.c_int32), ("n_tasks", ctypes.c_int64),
+                ("n_edges", ctypes.c_int64), ("max_critical_path", ctypes.c_int64), ("flops", ctypes.c_double)]
+
+
 class tqr_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
                 ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("tree", ctypes.c_int32), ("BS", ctypes.c_int32),
@@ -85,6 +90,10 @@ def lib():
             "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
             "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
             "tqr_set_trace": [vp, i32],
+            "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
+                                   ctypes.POINTER(vp)],
+            "tqr_batch_sync": [vp],
+            "tqr_batch_get_info": [vp, ctypes.POINTER(tqr_batch_info)],
             "tqr_get_trace": [vp, pi64, i64, pi64],
         }
         for name, args in sig.items():
@@ -97,6 +106,8 @@ def lib():
         L.tqr_inject_fault.restype = ctypes.c_int
         L.tqr_factor_noalloc.argtypes = [vp, i64, i64, i32, i32, pi32, i64, i32, vp, vp, vp, vp]
         L.tqr_factor_noalloc.restype = ctypes.c_int
+        L.tqr_batch_free.argtypes = [vp]
+        L.tqr_batch_free.restype = None
         L.tqr_free.argtypes = [vp]
         L.tqr_free.restype = None
         L.tqr_strerror.argtypes = [ctypes.c_int]
@@ -245,6 +256,81 @@ def tqr_form_t(f, T_geqrt=None, T_elim=None, stream=None):
     def p(t):
         return ctypes.c_void_p(t.data_ptr() if t is not None else None)
     _check(lib().tqr_form_t(ctypes.c_void_p(f.ptr), p(T_geqrt), p(T_elim), _stream(stream)), "tqr_form_t")
+
+
+class Batch:
+    """A tqr_batch handle; keeps the argument arrays alive for relaunches."""
+
+    def __init__(self, ptr, args, As):
+        self.ptr, self.args, self.As = ptr, args, As
+
+    def info(self):
+        return tqr_batch_get_info(self)
+
+    def free(self):
+        if self.ptr:
+            lib().tqr_batch_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _per_matrix(v, count, dtype):
+    a = np.asarray(v, dtype=dtype)
+    if a.ndim == 0:
+        a = np.full(count, a, dtype=dtype)
+    if a.shape != (count,):
+        raise ValueError("per-matrix parameter must be a scalar or have one entry per matrix")
+    return np.ascontiguousarray(a)
+
+
+def tqr_factor_batched(As, nb, ib, tree, BS=1, stream=None, reuse=None):
+    """Factor the column-major CUDA tensors in As in one launch; nb, ib, tree
+    and BS are scalars or one value per matrix.  ``reuse`` (a Batch built from
+    the same tensors and parameters) relaunches without allocation."""
+    count = len(As)
+    ptrs = (ctypes.c_void_p * count)()
+    m = np.zeros(count, dtype=np.int64)
+    n = np.zeros(count, dtype=np.int64)
+    for c, A in enumerate(As):
+        p, ld = _colmajor_ptr(A, "A[%d]" % c)
+        if ld != A.shape[0]:
+            raise ValueError("A[%d] must have leading dimension m" % c)
+        ptrs[c] = p.value
+        m[c], n[c] = A.shape
+    arrs = [_per_matrix(nb, count, np.int32), _per_matrix(ib, count, np.int32),
+            _per_matrix(tree, count, np.int32), _per_matrix(BS, count, np.int32)]
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    rc = lib().tqr_factor_batched(count, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), m.ctypes.data_as(P64),
+                                  n.ctypes.data_as(P64), *[a.ctypes.data_as(P32) for a in arrs], _stream(stream),
+                                  ctypes.byref(h))
+    _check(rc, "tqr_factor_batched")
+    if reuse is not None and h.value == reuse.ptr:
+        return reuse
+    return Batch(h.value, (ptrs, m, n, arrs), list(As))
+
+
+def tqr_batch_sync(b, raise_on_error=True):
+    rc = lib().tqr_batch_sync(ctypes.c_void_p(b.ptr))
+    if raise_on_error:
+        _check(rc, "tqr_batch_sync")
+    return rc
+
+
+def tqr_batch_get_info(b):
+    info = tqr_batch_info()
+    _check(lib().tqr_batch_get_info(ctypes.c_void_p(b.ptr), ctypes.byref(info)), "tqr_batch_get_info")
+    return {k: getattr(info, k) for k, _ in tqr_batch_info._fields_}
+
+
+def tqr_batch_free(b):
+    b.free()
 
 
 def tqr_set_trace(f, enable=True):
