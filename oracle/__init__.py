@@ -28,7 +28,7 @@ Notation follows the paper: tile rows ``i``, pivot rows ``piv``, panel columns
 
 # Tree identifiers.  The integer values are the same as the library's C enum
 # so that a test can name one tree for both sides; nothing else is shared.
-FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP = range(9)
+FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP, PLASMA_TS = range(10)
 TREE_NAMES = {
     FLAT_TS: "FlatTree-TS",
     FLAT_TT: "FlatTree-TT",
@@ -39,4 +39,5 @@ TREE_NAMES = {
     PLASMA: "PlasmaTree",
     ASAP: "ASAP",
     GRASAP: "GRASAP",
+    PLASMA_TS: "PlasmaTree-TS",
 }

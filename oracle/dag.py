@@ -35,7 +35,12 @@ WEIGHT = {GEQRT: 4, UNMQR: 6, TSQRT: 6, TSMQR: 12, TTQRT: 2, TTMQR: 6}
 
 
 def expand(p, q, elims, ts=False):
-    """Kernel tasks of an elimination list, in program (list) order."""
+    """Kernel tasks of an elimination list, in program (list) order.  ``ts``
+    is one kernel family for the whole list (True = TS) or one flag per
+    elimination."""
+    flags = [bool(ts)] * len(elims) if isinstance(ts, (bool, int)) else list(ts)
+    if len(flags) != len(elims):
+        raise ValueError("one TS flag per elimination")
     tasks = []
     triangle = set()
 
@@ -47,8 +52,10 @@ def expand(p, q, elims, ts=False):
         for j in range(k + 1, q + 1):
             tasks.append((UNMQR, x, 0, k, j))
 
-    for (i, piv, k) in elims:
-        if ts:
+    for (i, piv, k), use_ts in zip(elims, flags):
+        if use_ts:
+            if (i, k) in triangle:
+                raise ValueError("TS elimination of a tile already in triangle form")
             factor(piv, k)
             tasks.append((TSQRT, i, piv, k, 0))
             for j in range(k + 1, q + 1):

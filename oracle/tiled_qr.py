@@ -16,7 +16,6 @@ Tile (i,k) of the paper (1-based) is block ``[(i-1)*nb:i*nb, (k-1)*nb:k*nb]``.
 
 import numpy as np
 
-from . import FLAT_TS
 from . import dag
 from . import kernels
 from . import trees
@@ -65,7 +64,7 @@ def factor(A, nb, ib, tree, BS=1, elims=None, max_tasks=None):
     p, q = -(-m // nb), -(-n // nb)
     if elims is None:
         elims = trees.elimination_list(p, q, tree, BS)
-    ts = tree == FLAT_TS
+    ts = trees.ts_flags(tree, BS, elims)
     tasks = dag.expand(p, q, elims, ts)
     W = np.zeros((p * nb, q * nb))
     W[:m, :n] = A

@@ -8,7 +8,7 @@ Part of the test oracle (see ``oracle/__init__.py``).  Everything here is
 Readings of points the paper leaves open are stated beside each generator.
 """
 
-from . import FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP
+from . import FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP, PLASMA_TS
 
 
 # --------------------------------------------------------------------------
@@ -173,13 +173,31 @@ def elimination_list(p, q, tree, BS=1):
         return fibonacci(p, q)
     if tree == GREEDY:
         return greedy(p, q)
-    if tree == PLASMA:
+    if tree in (PLASMA, PLASMA_TS):
         return plasma_tree(p, q, BS)
     if tree == ASAP:
         return asap(p, q)
     if tree == GRASAP:
         return grasap(p, q, BS)
     raise ValueError("unknown tree %r" % (tree,))
+
+
+def ts_flags(tree, BS, elims):
+    """Kernel family of each elimination: True = TS (TSQRT/TSMQR), False = TT.
+
+    FlatTree-TS uses TS kernels throughout (Proposition 2).  PlasmaTree-TS is
+    PlasmaTree with TS kernels inside each domain -- the domain's first row
+    zeroes the others with the triangle-on-top-of-square kernels, as the
+    library the paper compares against does -- and TT kernels for the binary
+    merge of the domain heads.  Domains of column k start at row k, so rows i
+    and piv share a domain exactly when (i - k) // BS == (piv - k) // BS.
+    Every other tree uses TT kernels.
+    """
+    if tree == FLAT_TS:
+        return [True] * len(elims)
+    if tree == PLASMA_TS:
+        return [(i - k) // BS == (piv - k) // BS for (i, piv, k) in elims]
+    return [False] * len(elims)
 
 
 # --------------------------------------------------------------------------

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import (BINARY, FIBONACCI, FLAT_TS, FLAT_TT, GREEDY, PLASMA,
-                    SAMEH_KUCK)
+                    PLASMA_TS, SAMEH_KUCK)
 from oracle import kernels as K
 from oracle import tiled_qr as tq
 
@@ -104,7 +104,7 @@ def test_geqrt_single_tile_equals_lapack_geqrf():
 
 
 TREES = [(FLAT_TS, 1), (FLAT_TT, 1), (SAMEH_KUCK, 1), (BINARY, 1), (FIBONACCI, 1), (GREEDY, 1),
-         (PLASMA, 2), (PLASMA, 3)]
+         (PLASMA, 2), (PLASMA, 3), (PLASMA_TS, 2), (PLASMA_TS, 3)]
 
 
 @pytest.mark.parametrize("tree,BS", TREES)

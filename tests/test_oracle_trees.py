@@ -13,7 +13,7 @@ import pytest
 
 from conftest import load_blocks, load_rows
 from oracle import (BINARY, FIBONACCI, FLAT_TS, FLAT_TT, GREEDY, PLASMA,
-                    SAMEH_KUCK)
+                    PLASMA_TS, SAMEH_KUCK)
 from oracle import dag, trees
 
 TILED = {"FlatTree": (FLAT_TT, 1), "Fibonacci": (FIBONACCI, 1), "Greedy": (GREEDY, 1),
@@ -191,6 +191,62 @@ def test_plasma_extremes():
             assert trees.plasma_tree(p, q, p) == trees.sameh_kuck(p, q)
         assert (dag.critical_path(p, 1, trees.plasma_tree(p, 1, 1))
                 == dag.critical_path(p, 1, trees.binary_tree(p, 1)))
+
+
+def test_plasma_ts_extremes():
+    """PlasmaTree-TS with BS = p is FlatTree-TS (Proposition 2's critical
+    path: 6p - 2, 12p + 18q - 32, 30p - 34); with BS = 1 it has no domain
+    interior and is BinaryTree with TT kernels."""
+    for p in range(1, 16):
+        for q in range(1, p + 1):
+            el = trees.elimination_list(p, q, PLASMA_TS, p)
+            assert dag.expand(p, q, el, trees.ts_flags(PLASMA_TS, p, el)) == \
+                dag.expand(p, q, trees.sameh_kuck(p, q), True)
+            cp = dag.critical_path(p, q, el, trees.ts_flags(PLASMA_TS, p, el))
+            if q == 1:
+                assert cp == 6 * p - 2
+            elif p > q:
+                assert cp == 12 * p + 18 * q - 32
+            else:
+                assert cp == 30 * p - 34
+            el1 = trees.elimination_list(p, q, PLASMA_TS, 1)
+            assert not any(trees.ts_flags(PLASMA_TS, 1, el1))
+            assert dag.expand(p, q, el1, trees.ts_flags(PLASMA_TS, 1, el1)) == \
+                dag.expand(p, q, trees.plasma_tree(p, q, 1), False)
+
+
+def test_plasma_ts_hand_derived():
+    """p = 4, BS = 2, Table 1 weights.  Column 1: GEQRT(1) and GEQRT(3) at
+    0-4, TSQRT(2,1) and TSQRT(4,3) at 4-10, merge TTQRT(3,1) at 10-12, so
+    q = 1 ends at 12.  With q = 2 the updates UNMQR at 4-10 and TSMQR at
+    10-22 follow, TTMQR(3,1,2) runs 22-28; column 2 has domains {2,3} and
+    {4}: GEQRT(2,2) 22-26, TSQRT(3,2,2) 28-34 (after TTMQR wrote tile (3,2)),
+    GEQRT(4,2) 22-26 and the merge TTQRT(4,2,2) 34-36."""
+    el = trees.elimination_list(4, 1, PLASMA_TS, 2)
+    assert el == [(2, 1, 1), (4, 3, 1), (3, 1, 1)]
+    assert trees.ts_flags(PLASMA_TS, 2, el) == [True, True, False]
+    assert dag.critical_path(4, 1, el, trees.ts_flags(PLASMA_TS, 2, el)) == 12
+    el = trees.elimination_list(4, 2, PLASMA_TS, 2)
+    fl = trees.ts_flags(PLASMA_TS, 2, el)
+    assert fl == [True, True, False, True, False]
+    tasks = dag.expand(4, 2, el, fl)
+    _, cp = dag.simulate(tasks)
+    assert cp == 36
+    assert dag.total_weight(tasks) == 6 * 4 * 4 - 2 * 8
+    kinds = [t[0] for t in tasks]
+    assert kinds.count(dag.TSQRT) == 3 and kinds.count(dag.TTQRT) == 2 and kinds.count(dag.GEQRT) == 4
+    with pytest.raises(ValueError):          # TS on a tile already in triangle form
+        dag.expand(4, 1, el[:3], [True, True, True])
+
+
+@pytest.mark.parametrize("BS", [1, 2, 3, 5])
+def test_plasma_ts_weight_and_validity(BS):
+    for p in range(BS, 14):
+        for q in range(1, p + 1):
+            el = trees.elimination_list(p, q, PLASMA_TS, BS)
+            fl = trees.ts_flags(PLASMA_TS, BS, el)
+            assert trees.validate(p, q, el) is None
+            assert dag.total_weight(dag.expand(p, q, el, fl)) == 6 * p * q * q - 2 * q ** 3
 
 
 def test_example_list_of_section2():
