@@ -479,15 +479,120 @@ def batched_main(args):
     return 0
 
 
+# ------------------------------------------------------ per-tree comparison
+PLASMA_BS = (2, 4, 8, 16)
+
+
+def trees_main(args):
+    """The tree sweep for every tree: GFLOP/s per (tree, q) and the measured
+    makespan against the unit-weight critical path (Section 2.3 model),
+    converted to time at one SM's FP64 rate (nb^3/3 flop per unit).
+    PlasmaTree and PlasmaTree-TS take the fastest measured BS.  Each entry is
+    the median of ``--steps`` factorizations after one warm-up."""
+    import torch
+    import paper_1104_4475_gb300 as tqr
+    from paper_1104_4475_gb300 import build, workloads
+    build.build()
+    torch.cuda.set_device(0)
+    unit_s = NB ** 3 / 3.0 / (FP64_PEAK_TFLOPS * 1e12 / 152)
+    trees = [("FlatTree-TS", tqr.FLAT_TS), ("FlatTree-TT", tqr.FLAT_TT), ("BinaryTree", tqr.BINARY),
+             ("Fibonacci", tqr.FIBONACCI), ("Greedy", tqr.GREEDY), ("ASAP", tqr.ASAP),
+             ("PlasmaTree", tqr.PLASMA), ("PlasmaTree-TS", tqr.PLASMA_TS)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    t_all = time.perf_counter()
+    for q in QS:
+        src = torch.from_numpy(np.ascontiguousarray(workloads.uniform(M, NB * q, SEED).T)).cuda().t()
+        work = torch.empty_like(src.t()).t()
+        for name, tree in trees:
+            bss = [b for b in PLASMA_BS if b <= M // NB] if tree in (tqr.PLASMA, tqr.PLASMA_TS) else [1]
+            best = None
+            for BS in bss:
+                times, h = [], None
+                for rep in range(args.steps + 1):
+                    flush.fill_(1.0)
+                    work.copy_(src)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    h = tqr.tqr_factor(work, NB, IB, tree, BS, reuse=h)
+                    e1.record()
+                    tqr.tqr_sync(h)
+                    if rep > 0:
+                        times.append(e0.elapsed_time(e1) / 1e3)
+                cp = h.info()["critical_path"]
+                h.free()
+                t = statistics.median(times)
+                if best is None or t < best["ms"] / 1e3:
+                    best = {"BS": BS, "ms": 1e3 * t, "gflops": flops(M, NB * q) / t / 1e9,
+                            "critical_path_units": cp, "cp_bound_ms": 1e3 * cp * unit_s,
+                            "makespan_over_cp_bound": t / (cp * unit_s)}
+            out.setdefault(name, {})[str(q)] = best
+        del src, work
+    sweep = {name: workload_flops() / sum(v[str(q)]["ms"] / 1e3 for q in QS) / 1e9 for name, v in out.items()}
+    line = {"metric": "tiled-QR GFLOP/s (FP64) per tree", "value": max(sweep.values()), "unit": "GFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "FP64 tree sweep for every tree: m=16384 (p=64), nb=256, ib=32, n=256q, "
+                                   "q in {1,2,4,8,16,32,64}, U[-0.5,0.5]; PlasmaTree BS measured over "
+                                   "{2,4,8,16}", "l2": "256 MiB flush write before each factorization"},
+            "best_tree": max(sweep, key=sweep.get), "sweep_gflops": sweep, "per_tree": out,
+            "unit_ms": 1e3 * unit_s, "seconds": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------- learned cost model
+def costmodel_main(args):
+    """Trains the cost-model network on the GPU (the library's forward,
+    backward and Adam kernels) from the stored executor timings, then scores
+    its pick on the held-out shapes against the exhaustive best, the fixed
+    default (Greedy, nb 256) and the smallest-critical-path rule."""
+    import torch
+    from paper_1104_4475_gb300 import build, costmodel
+    build.build()
+    torch.cuda.set_device(0)
+    path = args.cost_data or os.path.join(ROOT, "paper_1104_4475_gb300", "data", "costmodel_timings_gb300.csv")
+    recs = costmodel.load_records(path)
+    train, test = costmodel.split(recs)
+    X, y = costmodel.design(train)
+    steps = 3000
+    costmodel.train(X[:64], y[:64], steps=10)                # warm-up (build, first launches)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    model, losses = costmodel.train(X, y, steps=steps)
+    e1.record()
+    torch.cuda.synchronize()
+    train_s = e0.elapsed_time(e1) / 1e3
+    fp64 = costmodel.summarize(costmodel.evaluate(model, test, 0))
+    lp = costmodel.summarize(costmodel.evaluate(model, test, 1))
+    Xt, yt = costmodel.design(test)
+    rmse = float(np.sqrt(np.mean((model.predict_log_seconds(Xt) - yt) ** 2)))
+    line = {"metric": "cost-model pick makespan / exhaustive best (held-out shapes, FP64)",
+            "value": fp64["model_over_best"], "unit": "x", "n_gpus": 1, "steps": steps, "warmup": 10,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "executor timings on GB300 (%d runs, %d shapes)" % (len(recs), len(costmodel.by_shape(recs))),
+            "config": {"workload": "3-layer MLP (width 64, FP32), full-batch Adam on %d training runs; m in "
+                                   "[4096,65536], n in [256,m], at most 5e11 flop per run; 12 FP64 and 6 "
+                                   "split-TF32 candidates per shape" % len(train)},
+            "detail": {"fp64": fp64, "split_tf32": lp, "test_rmse_log_seconds": rmse,
+                       "train_seconds": train_s, "train_steps_per_s": steps / train_s,
+                       "final_train_loss": losses[-1][1]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "lstsq", "batched"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "lstsq", "batched", "trees", "costmodel"],
                     help="sweep: FP64 tree sweep (default); lstsq: mixed-precision least squares; "
-                         "batched: 4096 tall-skinny matrices in one launch")
+                         "batched: 4096 tall-skinny matrices in one launch; trees: the sweep for every tree; "
+                         "costmodel: train and score the learned cost model")
+    ap.add_argument("--cost-data", default=None, help="executor timings CSV for --workload costmodel")
     ap.add_argument("--tune-db", default=None, help="autotune database to load, or to write after tuning")
     ap.add_argument("--tune-sample", type=int, default=32, help="matrices per size class when tuning")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -504,6 +609,10 @@ def main():
         return lstsq_main(args)
     if args.workload == "batched":
         return batched_main(args)
+    if args.workload == "trees":
+        return trees_main(args)
+    if args.workload == "costmodel":
+        return costmodel_main(args)
     return gpu_main(args)
 
 

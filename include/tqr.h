@@ -34,7 +34,10 @@ extern "C" {
 #endif
 
 /* Elimination trees (Section 3).  TQR_FLAT_TS runs FlatTree with TS kernels
- * (Proposition 2); every other tree runs TT kernels.  ASAP and GRASAP(k)
+ * (Proposition 2) and TQR_PLASMA_TS runs PlasmaTree with TS kernels inside
+ * each domain and TT kernels for the merge of the domain heads (the kernel
+ * mix of the TS-based library the experiments compare against); every other
+ * tree runs TT kernels.  ASAP and GRASAP(k)
  * (Section 3.2) are dynamic: their lists come from simulating the tiled time
  * model (Table 1 weights) while the list is built.  For TQR_GRASAP the BS
  * argument carries k, 0 <= k <= min(p,q) (0 = Greedy, min(p,q) = ASAP). */
@@ -47,7 +50,8 @@ typedef enum {
     TQR_GREEDY = 5,      /* Greedy for tiles (Algorithm 4)                 */
     TQR_PLASMA = 6,      /* PlasmaTree with domain size BS (Section 3.2)   */
     TQR_ASAP = 7,        /* ASAP: pair ready rows as soon as two are ready  */
-    TQR_GRASAP = 8       /* GRASAP(k), k = BS: Greedy, then ASAP on the last k columns */
+    TQR_GRASAP = 8,      /* GRASAP(k), k = BS: Greedy, then ASAP on the last k columns */
+    TQR_PLASMA_TS = 9    /* PlasmaTree(BS) list, TS inside domains, TT merges */
 } tqr_tree;
 
 /* Kernel kinds, as reported by tqr_tasks(). */
@@ -95,7 +99,7 @@ typedef struct {
     int32_t nb, ib;        /* tile size and inner blocking                 */
     int32_t p, q;          /* tile rows ceil(m/nb), tile columns ceil(n/nb) */
     int32_t tree, BS;      /* tree (-1 for a caller-given list), domain size */
-    int32_t ts;            /* 1 if TS kernels, 0 if TT                     */
+    int32_t ts;            /* 0 TT kernels, 1 TS kernels, 2 TS inside PlasmaTree domains + TT merges */
     int32_t strip;         /* columns per update task on the device        */
     int64_t n_elims;       /* length of the elimination list               */
     int64_t n_tile_tasks;  /* kernel tasks (Algorithms 2/3)                */
@@ -118,8 +122,9 @@ typedef struct {
  * padding).
  *   nb:   tile size, 8 <= nb <= 256, nb % 4 == 0.
  *   ib:   inner blocking, ib divides nb, ib <= 64.
- *   tree: a tqr_tree value.  BS: PlasmaTree domain size, 1 <= BS <= p, or
- *         the k of GRASAP(k), 0 <= k <= q (ignored by other trees).
+ *   tree: a tqr_tree value.  BS: PlasmaTree / PlasmaTree-TS domain size,
+ *         1 <= BS <= p, or the k of GRASAP(k), 0 <= k <= q (ignored by
+ *         other trees).
  *   out:  receives the handle.  If *out already holds a handle made for the
  *         same (m, n, nb, ib, tree, BS), its device buffers are reused and
  *         nothing is allocated; otherwise a new handle is created (the old
@@ -142,7 +147,9 @@ int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int
 /* Same with a caller-given elimination list: `list` (host) holds `count`
  * 0-based triplets (i, piv, k) in order; ts = 1 selects TS kernels, 0 TT.
  * The list is checked against the rules of Section 2.2 first
- * (TQR_ERR_INVALID_LIST).  *out is reused only if it was made from the same
+ * (TQR_ERR_INVALID_LIST); with ts = 1 a list that zeroes a tile already in
+ * triangle form (a row that was a pivot earlier in the same column) is
+ * invalid too, since TSQRT needs a square tile there.  *out is reused only if it was made from the same
  * list. */
 int tqr_factor_list(double* A, int64_t m, int64_t n, int nb, int ib, const int32_t* list,
                     int64_t count, int ts, void* stream, tqr_factors** out);
@@ -248,6 +255,29 @@ int tqr_batch_get_info(const tqr_batch* b, tqr_batch_info* info);
 void tqr_batch_free(tqr_batch* b);
 
 /* ---------------------------------------------------------------------------
+ * Cost-model network (the paper has no learned component; the autotuner uses
+ * it to rank configurations without timing them).  A 3-layer perceptron
+ * in -> 64 -> 64 -> 1 with ReLU, FP32.  Parameters are one device array of
+ * tqr_mlp_param_count(in) floats: W1 (64 x in, row-major), b1 (64), W2 (64 x
+ * 64, row-major), b2 (64), W3 (64), b3 (1).  X is B x in row-major (device).
+ *   tqr_mlp_forward:   y[s] = network(X[s]) for s < B.
+ *   tqr_mlp_loss_grad: loss (device scalar) = (1/B) sum_s (y[s] - t[s])^2 and
+ *                      its gradient w.r.t. the parameters into grad; work is a
+ *                      device scratch of B * (4*64 + 2) floats.  The gradient
+ *                      of every parameter is summed over samples in a fixed
+ *                      order (deterministic).
+ *   tqr_mlp_adam_step: one Adam update (bias-corrected, step >= 1) of count
+ *                      parameters with moment arrays m, v (device, zeroed
+ *                      before step 1). */
+#define TQR_MLP_MAX_IN 32
+int tqr_mlp_param_count(int in_dim);
+int tqr_mlp_forward(const float* params, int in_dim, const float* X, int B, float* y, void* stream);
+int tqr_mlp_loss_grad(const float* params, int in_dim, const float* X, const float* t, int B, float* work,
+                      float* grad, float* loss, void* stream);
+int tqr_mlp_adam_step(float* params, const float* grad, float* m, float* v, int count, float lr, float beta1,
+                      float beta2, float eps, int step, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Host-only integer entry points (no GPU needed).
  * ------------------------------------------------------------------------- */
 
@@ -310,7 +340,9 @@ int tqr_inject_fault(int kind);
  *   nb, ib: as for tqr_factor.
  *   list:  host, `count` 0-based triplets (i, piv, k), e.g. from
  *          tqr_elimination_list(); checked against the Section 2.2 rules
- *          (TQR_ERR_INVALID_LIST).  ts = 1: TS kernels, 0: TT kernels.
+ *          (TQR_ERR_INVALID_LIST).  ts = 1: TS kernels, 0: TT kernels;
+ *          with ts = 1, zeroing a tile already in triangle form is also
+ *          TQR_ERR_INVALID_LIST.
  *   tau_geqrt, tau_elim: device outputs, p*q*nb doubles each; the tau of
  *          reflector r of GEQRT(i,k) (resp. of the TTQRT/TSQRT zeroing tile
  *          (i,k)) is stored at [((size_t)k*p + i)*nb + r].

@@ -1,0 +1,280 @@
+"""Learned cost model: predicts the makespan of a factorization from
+(m, n, nb, ib, tree, BS, precision) so that a configuration can be chosen
+without timing every candidate.
+
+* Network: the library's 3-layer perceptron (in -> 64 -> 64 -> 1, ReLU, FP32),
+  trained on the GPU by the CUDA kernels behind tqr_mlp_loss_grad /
+  tqr_mlp_adam_step on log(seconds).
+* Features: log sizes, tile counts, ib/nb, one-hot tree, BS relative to p,
+  one-hot precision, plus the LAPACK flop count and the unit-weight critical
+  path from the host simulator (tqr_critical_path), both in log scale.
+* Data: wall times of the executor itself (CUDA events around tqr_factor_ex),
+  collected by :func:`collect`.
+
+Command line:
+  python -m paper_1104_4475_gb300.costmodel collect --shapes 120 --out timings.csv
+  python -m paper_1104_4475_gb300.costmodel evaluate --data timings.csv
+"""
+
+import argparse
+import csv
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import tqr
+
+TREE_IDS = list(range(9))
+FP64_CONFIGS = [(nb, 32, tree, None) for nb in (128, 256)
+                for tree in (tqr.GREEDY, tqr.BINARY, tqr.FIBONACCI, tqr.FLAT_TT, tqr.FLAT_TS, tqr.PLASMA)]
+LP_CONFIGS = [(256, 32, tree, None) for tree in (tqr.GREEDY, tqr.BINARY, tqr.FIBONACCI, tqr.FLAT_TT, tqr.FLAT_TS,
+                                                 tqr.PLASMA)]
+DEFAULT = (256, 32, tqr.GREEDY, 1, 0)        # the configuration used without a model
+FEATURES = 22
+
+
+def plasma_bs(m, nb):
+    return max(1, -(-m // nb) // 8)
+
+
+def features(m, n, nb, ib, tree, BS, prec):
+    p, q = -(-m // nb), -(-n // nb)
+    cp = tqr.tqr_critical_path(p, q, tree, BS)
+    flops = 2.0 * n * n * (m - n / 3.0)
+    f = [math.log2(m) / 16, math.log2(n) / 16, math.log2(nb) / 8, ib / nb, math.log2(p) / 9, math.log2(q) / 9]
+    f += [1.0 if tree == t else 0.0 for t in TREE_IDS]
+    f += [BS / p if tree in (tqr.PLASMA, tqr.GRASAP) else 0.0]
+    f += [1.0 if prec == k else 0.0 for k in range(3)]
+    f += [math.log2(flops) / 48, math.log2(cp * nb ** 3 / 3.0) / 48, math.log2(cp) / 12]
+    assert len(f) == FEATURES
+    return np.array(f, dtype=np.float32)
+
+
+def configs_for(m, with_lp=True):
+    out = []
+    for nb, ib, tree, _ in FP64_CONFIGS:
+        out.append((nb, ib, tree, plasma_bs(m, nb) if tree == tqr.PLASMA else 1, 0))
+    if with_lp:
+        for nb, ib, tree, _ in LP_CONFIGS:
+            out.append((nb, ib, tree, plasma_bs(m, nb) if tree == tqr.PLASMA else 1, 1))
+    return out
+
+
+def random_shapes(count, seed, m_range=(4096, 65536), n_range=(256, 8192), max_flops=5e11):
+    """Log-uniform shapes with n <= m and at most max_flops LAPACK flops."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        m = int(2 ** rng.uniform(math.log2(m_range[0]), math.log2(m_range[1])))
+        n = int(2 ** rng.uniform(math.log2(n_range[0]), math.log2(min(n_range[1], m))))
+        m, n = m // 64 * 64, max(256, n // 64 * 64)
+        if n <= m and 2.0 * n * n * (m - n / 3.0) <= max_flops:
+            out.append((m, n))
+    return out
+
+
+def collect(shapes, with_lp=True, log=None, seed=1):
+    """Time every candidate configuration on each shape with CUDA events
+    around tqr_factor_ex (the second of two runs, so the cached plan is
+    reused as in steady use); returns a list of records."""
+    import torch
+    from . import build
+    build.build()
+    recs = []
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    for si, (m, n) in enumerate(shapes):
+        src = (torch.rand(n, m, generator=g, dtype=torch.float64, device="cuda") - 0.5).t()
+        work = torch.empty_like(src.t()).t()
+        for cfg in configs_for(m, with_lp):
+            nb, ib, tree, BS, prec = cfg
+            for rep in range(2):
+                work.copy_(src)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f = tqr.tqr_factor_ex(work, nb, ib, tree, BS, prec)
+                e1.record()
+                tqr.tqr_sync(f)
+                secs = e0.elapsed_time(e1) / 1e3
+                f.free()
+            recs.append({"shape": si, "m": m, "n": n, "nb": nb, "ib": ib, "tree": tree, "BS": BS, "prec": prec,
+                         "seconds": secs})
+        if log:
+            log("shape %d/%d (%d x %d) done" % (si + 1, len(shapes), m, n))
+        del src, work
+    return recs
+
+
+def save_records(recs, path):
+    with open(path, "w", newline="") as fh:
+        w = csv.DictWriter(fh, fieldnames=["shape", "m", "n", "nb", "ib", "tree", "BS", "prec", "seconds"])
+        w.writeheader()
+        for r in recs:
+            w.writerow(r)
+
+
+def load_records(path):
+    out = []
+    with open(path) as fh:
+        for r in csv.DictReader(fh):
+            out.append({k: (float(v) if k == "seconds" else int(v)) for k, v in r.items()})
+    return out
+
+
+def design(recs):
+    X = np.stack([features(r["m"], r["n"], r["nb"], r["ib"], r["tree"], r["BS"], r["prec"]) for r in recs])
+    y = np.log(np.array([r["seconds"] for r in recs], dtype=np.float64)).astype(np.float32)
+    return X, y
+
+
+def init_params(d, seed=0):
+    """He-style initialization, flat in the library's parameter order."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((64, d)) * np.sqrt(2.0 / d)
+    W2 = rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64)
+    W3 = rng.standard_normal(64) * np.sqrt(1.0 / 64)
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3, [0.0]]).astype(np.float32)
+
+
+class Model:
+    """Feature standardization + network parameters (a CUDA float32 tensor)."""
+
+    def __init__(self, params, mu, sd, ymu):
+        self.params, self.mu, self.sd, self.ymu = params, mu, sd, ymu
+
+    def predict_log_seconds(self, X):
+        import torch
+        Xs = torch.from_numpy(((X - self.mu) / self.sd).astype(np.float32)).cuda()
+        y = tqr.tqr_mlp_forward(self.params, Xs)
+        return y.cpu().numpy().astype(np.float64) + self.ymu
+
+    def to_json(self):
+        return {"version": 1, "features": FEATURES, "params": self.params.cpu().numpy().tolist(),
+                "mu": self.mu.tolist(), "sd": self.sd.tolist(), "ymu": self.ymu}
+
+    @staticmethod
+    def from_json(d):
+        import torch
+        return Model(torch.tensor(d["params"], dtype=torch.float32, device="cuda"), np.array(d["mu"], np.float32),
+                     np.array(d["sd"], np.float32), float(d["ymu"]))
+
+
+def train(X, y, steps=3000, lr=3e-3, seed=0, log_every=0, log=None):
+    """Full-batch Adam on the GPU with the library's kernels; returns (Model, losses)."""
+    import torch
+    mu = X.mean(axis=0)
+    sd = X.std(axis=0) + 1e-3
+    ymu = float(y.mean())
+    Xs = torch.from_numpy(((X - mu) / sd).astype(np.float32)).cuda()
+    ts = torch.from_numpy((y - ymu).astype(np.float32)).cuda()
+    params = torch.from_numpy(init_params(X.shape[1], seed)).cuda()
+    grad = torch.zeros_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(Xs.shape[0] * (4 * 64 + 2), dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(1, steps + 1):
+        tqr.tqr_mlp_loss_grad(params, Xs, ts, grad, loss, work)
+        tqr.tqr_mlp_adam_step(params, grad, m, v, lr, step)
+        if step % 100 == 0 or step == 1:
+            losses.append((step, float(loss.item())))
+            if log and log_every and step % log_every == 0:
+                log("step %d loss %.4f" % (step, losses[-1][1]))
+    return Model(params, mu, sd, ymu), losses
+
+
+def pick(model, m, n, precisions=(0,)):
+    """The candidate (nb, ib, tree, BS, precision) with the smallest predicted
+    makespan for an m x n factorization (no timing); exhaustive timing
+    (:func:`collect`) stays the fallback and the judge of this choice."""
+    cands = [c for c in configs_for(m, with_lp=True) if c[4] in precisions]
+    X = np.stack([features(m, n, *c) for c in cands])
+    return cands[int(np.argmin(model.predict_log_seconds(X)))]
+
+
+def by_shape(recs):
+    out = {}
+    for r in recs:
+        out.setdefault(r["shape"], []).append(r)
+    return out
+
+
+def evaluate(model, recs, prec=0):
+    """For each shape: measured time of the model's pick among the timed
+    candidates of that precision, of the exhaustive best, of the fixed default
+    and of the smallest-critical-path pick."""
+    rows = []
+    for sid, rs in by_shape(recs).items():
+        rs = [r for r in rs if r["prec"] == prec]
+        if not rs:
+            continue
+        X, _ = design(rs)
+        pred = model.predict_log_seconds(X)
+        t = np.array([r["seconds"] for r in rs])
+        best = t.min()
+        pick = t[int(np.argmin(pred))]
+        dflt = [r["seconds"] for r in rs if (r["nb"], r["ib"], r["tree"]) == DEFAULT[:3]]
+        cps = [tqr.tqr_critical_path(-(-r["m"] // r["nb"]), -(-r["n"] // r["nb"]), r["tree"], r["BS"])
+               * r["nb"] ** 3 for r in rs]
+        rows.append({"shape": sid, "m": rs[0]["m"], "n": rs[0]["n"], "best": best, "model": pick / best,
+                     "default": (dflt[0] / best) if dflt else float("nan"),
+                     "min_cp": t[int(np.argmin(cps))] / best, "exact": bool(pick == best)})
+    return rows
+
+
+def split(recs, holdout_frac=0.25, seed=0):
+    shapes = sorted(by_shape(recs))
+    rng = np.random.default_rng(seed)
+    rng.shuffle(shapes)
+    k = max(1, int(round(len(shapes) * holdout_frac)))
+    test = set(shapes[:k])
+    return [r for r in recs if r["shape"] not in test], [r for r in recs if r["shape"] in test]
+
+
+def summarize(rows):
+    a = lambda key: float(np.mean([r[key] for r in rows]))
+    return {"shapes": len(rows), "model_over_best": a("model"), "default_over_best": a("default"),
+            "min_cp_over_best": a("min_cp"), "model_exact_fraction": float(np.mean([r["exact"] for r in rows])),
+            "model_worst": float(max(r["model"] for r in rows))}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--shapes", type=int, default=120)
+    c.add_argument("--seed", type=int, default=11)
+    c.add_argument("--out", required=True)
+    e = sub.add_parser("evaluate")
+    e.add_argument("--data", required=True)
+    e.add_argument("--steps", type=int, default=3000)
+    e.add_argument("--model-out", default=None)
+    a = ap.parse_args(argv)
+    if a.cmd == "collect":
+        t0 = time.time()
+        recs = collect(random_shapes(a.shapes, a.seed), log=lambda s: print(s, file=sys.stderr, flush=True))
+        save_records(recs, a.out)
+        print(json.dumps({"records": len(recs), "seconds": time.time() - t0}))
+    else:
+        recs = load_records(a.data)
+        tr, te = split(recs)
+        X, y = design(tr)
+        model, losses = train(X, y, steps=a.steps)
+        Xt, yt = design(te)
+        rmse = float(np.sqrt(np.mean((model.predict_log_seconds(Xt) - yt) ** 2)))
+        out = {"train_records": len(tr), "test_records": len(te), "final_train_loss": losses[-1][1],
+               "test_rmse_log_seconds": rmse, "fp64": summarize(evaluate(model, te, 0))}
+        if any(r["prec"] == 1 for r in te):
+            out["split_tf32"] = summarize(evaluate(model, te, 1))
+        if a.model_out:
+            with open(a.model_out, "w") as fh:
+                json.dump(model.to_json(), fh)
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

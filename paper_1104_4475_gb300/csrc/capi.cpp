@@ -69,7 +69,7 @@ struct PlanKey {
 struct Plan {
     PlanKey key;
     int p = 0, q = 0, G = 0, W = 0, smem = 0;
-    bool ts = false;
+    int ts = 0;                // 0 TT, 1 TS, 2 TS inside PlasmaTree domains
     std::vector<Elim> elims;
     std::vector<TileTask> tt;
     int64_t cp = 0;
@@ -88,6 +88,12 @@ static std::map<PlanKey, std::shared_ptr<Plan>>& plans() {
     return *m;
 }
 
+// Trees whose BS argument matters (PlasmaTree domain size, GRASAP's k).
+static bool uses_bs(int tree) { return tree == TQR_PLASMA || tree == TQR_PLASMA_TS || tree == TQR_GRASAP; }
+
+// Kernel family recorded in the plan key: 0 TT, 1 TS, 2 TS inside domains.
+static int kernel_mode(int tree) { return tree == TQR_FLAT_TS ? 1 : tree == TQR_PLASMA_TS ? 2 : 0; }
+
 static double lapack_flops(int64_t m, int64_t n) {
     const double M = static_cast<double>(m), N = static_cast<double>(n);
     return 2.0 * N * N * (M - N / 3.0);
@@ -98,7 +104,7 @@ static int make_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
     P->key = key;
     P->p = static_cast<int>((key.m + key.nb - 1) / key.nb);
     P->q = static_cast<int>((key.n + key.nb - 1) / key.nb);
-    P->ts = key.ts != 0;
+    P->ts = key.ts;
     if (key.tree >= 0) {
         int rc = make_elims(P->p, P->q, key.tree, key.BS, P->elims);
         if (rc != TQR_OK) return rc;
@@ -107,7 +113,9 @@ static int make_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
     }
     if (validate_elims(P->p, P->q, P->elims.data(), static_cast<int64_t>(P->elims.size())) != TQR_OK)
         return TQR_ERR_INVALID_LIST;
-    expand_tasks(P->p, P->q, P->elims, P->ts, P->tt);
+    const std::vector<char> ts_of = key.tree >= 0 ? ts_flags(key.tree, key.BS, P->elims)
+                                                  : std::vector<char>(P->elims.size(), key.ts ? 1 : 0);
+    if (!expand_tasks(P->p, P->q, P->elims, ts_of, P->tt)) return TQR_ERR_INVALID_LIST;
     P->cp = simulate(P->p, P->q, P->tt, nullptr);
     if (!choose_layout(key.nb, key.ib, &P->G, &P->smem)) return TQR_ERR_UNSUPPORTED;
     P->W = strip_width(P->G);
@@ -219,7 +227,7 @@ static int host_plan(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int
     int rc = make_elims(H->p, H->q, tree, BS, el);
     if (rc != TQR_OK) return rc;
     std::vector<TileTask> tt;
-    expand_tasks(H->p, H->q, el, tree == TQR_FLAT_TS, tt);
+    if (!expand_tasks(H->p, H->q, el, ts_flags(tree, BS, el), tt)) return TQR_ERR_INVALID_LIST;
     H->cp = simulate(H->p, H->q, tt, nullptr);
     build_factor_graph(H->p, H->q, nb, W, static_cast<int>(n - static_cast<int64_t>(H->q - 1) * nb), tt, H->g);
     std::lock_guard<std::mutex> lk(g_hplans_mu);
@@ -415,16 +423,16 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
     try {
         int rc = check_common(A, m, n, nb, ib);
         if (rc != TQR_OK) return rc;
-        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -6;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
         const int p = static_cast<int>((m + nb - 1) / nb);
         const int q = static_cast<int>((n + nb - 1) / nb);
-        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -7;
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
         if (!out) return -9;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
         PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
-                    (tree == TQR_PLASMA || tree == TQR_GRASAP) ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
+                    uses_bs(tree) ? BS : 0, kernel_mode(tree), dev, {}};
         return run_factor(key, A, stream, out);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
@@ -438,17 +446,17 @@ int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int
     try {
         int rc = check_common(A, m, n, nb, ib);
         if (rc != TQR_OK) return rc;
-        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -6;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
         const int p = static_cast<int>((m + nb - 1) / nb);
         const int q = static_cast<int>((n + nb - 1) / nb);
-        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -7;
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
         if (precision < TQR_FP64 || precision > TQR_TF32) return -8;
         if (!out) return -10;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
         PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
-                    (tree == TQR_PLASMA || tree == TQR_GRASAP) ? BS : 0, tree == TQR_FLAT_TS ? 1 : 0, dev, {}};
+                    uses_bs(tree) ? BS : 0, kernel_mode(tree), dev, {}};
         return run_factor(key, A, stream, out, precision);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
@@ -597,7 +605,7 @@ int tqr_get_info(const tqr_factors* f, tqr_info* info) {
     info->q = P.q;
     info->tree = P.key.tree;
     info->BS = P.key.BS;
-    info->ts = P.ts ? 1 : 0;
+    info->ts = P.ts;
     info->strip = P.W;
     info->n_elims = static_cast<int64_t>(P.elims.size());
     info->n_tile_tasks = static_cast<int64_t>(P.tt.size());
@@ -670,8 +678,8 @@ int tqr_elimination_list(int p, int q, int tree, int BS, int32_t* out, int64_t c
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
-        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -3;
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -4;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!count) return -7;
         std::vector<Elim> el;
@@ -709,15 +717,15 @@ int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
-        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -3;
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -4;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!cp) return -5;
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
         if (rc != TQR_OK) return rc;
         std::vector<TileTask> tt;
-        expand_tasks(p, q, el, tree == TQR_FLAT_TS, tt);
+        if (!expand_tasks(p, q, el, ts_flags(tree, BS, el), tt)) return TQR_ERR_INTERNAL;
         std::vector<int64_t> fin;
         *cp = simulate(p, q, tt, &fin);
         if (zero_time) {
@@ -736,15 +744,15 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
     try {
         if (p < 1 || p > 65535) return -1;
         if (q < 1 || q > p) return -2;
-        if (tree < TQR_FLAT_TS || tree > TQR_GRASAP) return -3;
-        if (tree == TQR_PLASMA && (BS < 1 || BS > p)) return -4;
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -3;
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -4;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!count) return -8;
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
         if (rc != TQR_OK) return rc;
         std::vector<TileTask> tt;
-        expand_tasks(p, q, el, tree == TQR_FLAT_TS, tt);
+        if (!expand_tasks(p, q, el, ts_flags(tree, BS, el), tt)) return TQR_ERR_INTERNAL;
         *count = static_cast<int64_t>(tt.size());
         if (static_cast<int64_t>(tt.size()) > cap) return TQR_ERR_CAPACITY;
         if (!out && !tt.empty()) return -5;
@@ -805,10 +813,10 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
         for (int c = 0; c < count; ++c) {
             const int rc = check_common(A[c], m[c], n[c], nb[c], ib[c]);
             if (rc != TQR_OK) return rc == -1 ? -2 : (rc == -2 ? -3 : (rc == -3 ? -4 : (rc == -4 ? -5 : -6)));
-            if (tree[c] < TQR_FLAT_TS || tree[c] > TQR_GRASAP) return -7;
+            if (tree[c] < TQR_FLAT_TS || tree[c] > TQR_PLASMA_TS) return -7;
             const int p = static_cast<int>((m[c] + nb[c] - 1) / nb[c]);
             const int q = static_cast<int>((n[c] + nb[c] - 1) / nb[c]);
-            if (tree[c] == TQR_PLASMA && (BS[c] < 1 || BS[c] > p)) return -8;
+            if ((tree[c] == TQR_PLASMA || tree[c] == TQR_PLASMA_TS) && (BS[c] < 1 || BS[c] > p)) return -8;
             if (tree[c] == TQR_GRASAP && (BS[c] < 0 || BS[c] > q)) return -8;
             nbmax = std::max(nbmax, nb[c]);
             ibmax = std::max(ibmax, ib[c]);
@@ -835,7 +843,7 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
         int64_t tau_off = 0;
         for (int c = 0; c < count; ++c) {
             const int t = tree[c] == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree[c];
-            const int bs = (t == TQR_PLASMA || t == TQR_GRASAP) ? BS[c] : 0;
+            const int bs = uses_bs(t) ? BS[c] : 0;
             std::shared_ptr<HostPlan> H;
             const int rc = host_plan(m[c], n[c], nb[c], ib[c], t, bs, W, H);
             if (rc != TQR_OK) return rc;

@@ -126,6 +126,7 @@ public:
         for (int t = 0; t < p_ * q_ * 2; ++t) g_h.prod[t] = -1;
         for (int64_t e = 0; e < count; ++e) {
             const int i = list[3 * e], piv = list[3 * e + 1], k = list[3 * e + 2];
+            if (ts_ && g_h.tri[k * p_ + i]) return TQR_ERR_INVALID_LIST;   // TS needs a square tile
             if (!factor(piv, k) || (!ts_ && !factor(i, k))) return TQR_ERR_TOO_LARGE;
             if (!panel(ts_ ? TSQRT : TTQRT, i, piv, k)) return TQR_ERR_TOO_LARGE;
             for (int j = k + 1; j < q_; ++j)

@@ -239,6 +239,7 @@ int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out) {
         case TQR_FIBONACCI: fibonacci_list(p, q, out); return TQR_OK;
         case TQR_GREEDY: greedy_list(p, q, out); return TQR_OK;
         case TQR_PLASMA:
+        case TQR_PLASMA_TS:
             if (BS < 1 || BS > p) return -4;
             plasma_list(p, q, BS, out);
             return TQR_OK;
@@ -286,7 +287,27 @@ int validate_elims(int p, int q, const Elim* e, int64_t count) {
 // tile of the last column of a square matrix, which takes part in no
 // elimination, is factored at the end.
 // ---------------------------------------------------------------------------
-void expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out) {
+// Kernel family per elimination (1 = TS, 0 = TT).  FlatTree-TS is TS
+// throughout; PlasmaTree-TS uses TS when row i lies in its pivot's domain
+// (domains of column k start at row k, BS rows each) and TT for the merges of
+// domain heads; every other tree is TT.
+std::vector<char> ts_flags(int tree, int BS, const std::vector<Elim>& elims) {
+    std::vector<char> f(elims.size(), tree == TQR_FLAT_TS ? 1 : 0);
+    if (tree == TQR_PLASMA_TS)
+        for (size_t t = 0; t < elims.size(); ++t)
+            f[t] = (elims[t].i - elims[t].k) / BS == (elims[t].piv - elims[t].k) / BS;
+    return f;
+}
+
+bool expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out) {
+    return expand_tasks(p, q, elims, std::vector<char>(elims.size(), ts ? 1 : 0), out);
+}
+
+// Returns false when a TS elimination meets a tile already in triangle form
+// (a row that was a pivot earlier in the same column): the TS kernels need a
+// square tile there, so such a list is invalid for them.
+bool expand_tasks(int p, int q, const std::vector<Elim>& elims, const std::vector<char>& ts_of,
+                  std::vector<TileTask>& out) {
     out.clear();
     std::vector<char> tri(static_cast<size_t>(p) * q, 0);
     auto factor = [&](int x, int k) {
@@ -296,13 +317,17 @@ void expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::ve
         out.push_back({GEQRT, x, -1, k, -1});
         for (int j = k + 1; j < q; ++j) out.push_back({UNMQR, x, -1, k, j});
     };
-    for (const Elim& e : elims) {
+    for (size_t t = 0; t < elims.size(); ++t) {
+        const Elim& e = elims[t];
+        const bool ts = ts_of[t] != 0;
+        if (ts && tri[static_cast<size_t>(e.k) * p + e.i]) return false;
         factor(e.piv, e.k);
         if (!ts) factor(e.i, e.k);
         out.push_back({ts ? TSQRT : TTQRT, e.i, e.piv, e.k, -1});
         for (int j = e.k + 1; j < q; ++j) out.push_back({ts ? TSMQR : TTMQR, e.i, e.piv, e.k, j});
     }
     for (int k = 0; k < std::min(p, q); ++k) factor(k, k);
+    return true;
 }
 
 // Dependencies of tile tasks: the producer of the reflectors a task applies,

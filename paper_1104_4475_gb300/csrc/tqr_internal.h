@@ -43,7 +43,10 @@ struct MatDesc {
 // ---- host planner (planner.cpp) ----
 int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out);
 int validate_elims(int p, int q, const Elim* e, int64_t count);
-void expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out);
+bool expand_tasks(int p, int q, const std::vector<Elim>& elims, bool ts, std::vector<TileTask>& out);
+bool expand_tasks(int p, int q, const std::vector<Elim>& elims, const std::vector<char>& ts_of,
+                  std::vector<TileTask>& out);
+std::vector<char> ts_flags(int tree, int BS, const std::vector<Elim>& elims);
 // Unit-weight ASAP finish time of every tile task and the critical path.
 int64_t simulate(int p, int q, const std::vector<TileTask>& tasks, std::vector<int64_t>* finish);
 

@@ -18,9 +18,10 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 GEQRT, UNMQR, TTQRT, TTMQR, TSQRT, TSMQR = range(6)
-FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP = range(9)
+FLAT_TS, FLAT_TT, SAMEH_KUCK, BINARY, FIBONACCI, GREEDY, PLASMA, ASAP, GRASAP, PLASMA_TS = range(10)
 TREES = {"flat_ts": FLAT_TS, "flat_tt": FLAT_TT, "sameh_kuck": SAMEH_KUCK, "binary": BINARY,
-         "fibonacci": FIBONACCI, "greedy": GREEDY, "plasma": PLASMA, "asap": ASAP, "grasap": GRASAP}
+         "fibonacci": FIBONACCI, "greedy": GREEDY, "plasma": PLASMA, "asap": ASAP, "grasap": GRASAP,
+         "plasma_ts": PLASMA_TS}
 
 TQR_ERR_INVALID_LIST = -100
 TQR_ERR_TIMEOUT = -101
@@ -93,6 +94,11 @@ def lib():
             "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
                                    ctypes.POINTER(vp)],
             "tqr_batch_sync": [vp],
+            "tqr_mlp_param_count": [i32],
+            "tqr_mlp_forward": [vp, i32, vp, i32, vp, vp],
+            "tqr_mlp_loss_grad": [vp, i32, vp, vp, i32, vp, vp, vp, vp],
+            "tqr_mlp_adam_step": [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, i32, vp],
             "tqr_batch_get_info": [vp, ctypes.POINTER(tqr_batch_info)],
             "tqr_get_trace": [vp, pi64, i64, pi64],
         }
@@ -331,6 +337,42 @@ def tqr_batch_get_info(b):
 
 def tqr_batch_free(b):
     b.free()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tqr_mlp_param_count(in_dim):
+    n = lib().tqr_mlp_param_count(int(in_dim))
+    if n < 0:
+        raise TqrError(n, "tqr_mlp_param_count")
+    return n
+
+
+def tqr_mlp_forward(params, X, y=None, stream=None):
+    """Network outputs for the rows of X (float32 CUDA tensors)."""
+    import torch
+    B, d = X.shape
+    if y is None:
+        y = torch.empty(B, dtype=torch.float32, device=X.device)
+    _check(lib().tqr_mlp_forward(_ptr(params), d, _ptr(X), B, _ptr(y), _stream(stream)), "tqr_mlp_forward")
+    return y
+
+
+def tqr_mlp_loss_grad(params, X, t, grad, loss, work=None, stream=None):
+    import torch
+    B, d = X.shape
+    if work is None:
+        work = torch.empty(B * (4 * 64 + 2), dtype=torch.float32, device=X.device)
+    _check(lib().tqr_mlp_loss_grad(_ptr(params), d, _ptr(X), _ptr(t), B, _ptr(work), _ptr(grad), _ptr(loss),
+                                   _stream(stream)), "tqr_mlp_loss_grad")
+    return work
+
+
+def tqr_mlp_adam_step(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().tqr_mlp_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), lr, beta1, beta2,
+                                   eps, int(step), _stream(stream)), "tqr_mlp_adam_step")
 
 
 def tqr_set_trace(f, enable=True):

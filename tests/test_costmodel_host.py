@@ -1,0 +1,64 @@
+"""Host logic of the learned cost model: features, candidates, shapes, data
+split and the stored timing set (no GPU)."""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_1104_4475_gb300 import costmodel, tqr
+
+DATA = os.path.join(os.path.dirname(costmodel.__file__), "data", "costmodel_timings_gb300.csv")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1104_4475_gb300 import build
+    build.build()
+
+
+def test_features_shape_and_encoding():
+    f = costmodel.features(16384, 2048, 256, 32, tqr.PLASMA, 8, 1)
+    assert f.shape == (costmodel.FEATURES,) and f.dtype == np.float32
+    assert costmodel.FEATURES <= 32                   # the network's input limit
+    trees = f[6:15]
+    assert trees.sum() == 1 and trees[tqr.PLASMA] == 1
+    assert f[15] == pytest.approx(8 / 64)             # BS / p
+    assert list(f[16:19]) == [0, 1, 0]                # precision one-hot
+    # the critical-path feature comes from the library's simulator
+    cp = tqr.tqr_critical_path(64, 8, tqr.PLASMA, 8)
+    assert f[21] == pytest.approx(np.log2(cp) / 12)
+
+
+def test_candidates_and_shapes():
+    c = costmodel.configs_for(20000)
+    assert len(c) == 18 and len(set(c)) == 18
+    assert all(BS == 1 for (nb, ib, tree, BS, prec) in c if tree != tqr.PLASMA)
+    assert costmodel.DEFAULT in c
+    shapes = costmodel.random_shapes(50, 3)
+    assert shapes == costmodel.random_shapes(50, 3)
+    for m, n in shapes:
+        assert 4096 <= m <= 65536 and 256 <= n <= m and m % 64 == 0 and n % 64 == 0
+        assert 2.0 * n * n * (m - n / 3.0) <= 5e11
+
+
+def test_stored_timings_and_split():
+    recs = costmodel.load_records(DATA)
+    shapes = costmodel.by_shape(recs)
+    assert len(recs) == 1800 and len(shapes) == 100
+    for sid, rs in shapes.items():
+        assert sorted((r["nb"], r["ib"], r["tree"], r["BS"], r["prec"]) for r in rs) == \
+            sorted(costmodel.configs_for(rs[0]["m"]))
+        assert all(r["seconds"] > 0 for r in rs)
+    tr, te = costmodel.split(recs)
+    assert len(tr) + len(te) == len(recs)
+    assert not {r["shape"] for r in tr} & {r["shape"] for r in te}
+    assert costmodel.split(recs)[1] == te               # deterministic
+
+
+def test_records_roundtrip(tmp_path):
+    recs = [{"shape": 0, "m": 4096, "n": 256, "nb": 128, "ib": 32, "tree": 5, "BS": 1, "prec": 0,
+             "seconds": 0.0125}]
+    p = tmp_path / "t.csv"
+    costmodel.save_records(recs, str(p))
+    assert costmodel.load_records(str(p)) == recs

@@ -105,7 +105,7 @@ def test_small_config_parity():
 
 TREES = [(tqr.FLAT_TS, 1), (tqr.FLAT_TT, 1), (tqr.SAMEH_KUCK, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1),
          (tqr.GREEDY, 1), (tqr.PLASMA, 1), (tqr.PLASMA, 3), (tqr.PLASMA, 10), (tqr.ASAP, 1),
-         (tqr.GRASAP, 2)]
+         (tqr.GRASAP, 2), (tqr.PLASMA_TS, 1), (tqr.PLASMA_TS, 3), (tqr.PLASMA_TS, 10)]
 
 
 @pytest.mark.parametrize("tree,BS", TREES)
@@ -131,11 +131,13 @@ def test_every_tree_ragged(tree, BS):
     (1536, 512, 256, 32, tqr.GREEDY),   # nb 256: four strips per tile column
     (2000, 700, 256, 32, tqr.FLAT_TS),  # nb 256, ragged
     (700, 300, 48, 16, tqr.GREEDY),     # nb not a power of two
+    (2000, 700, 256, 32, tqr.PLASMA_TS),  # TS domains + TT merges, nb 256, ragged
 ])
 def test_shapes(m, n, nb, ib, tree):
     A = workloads.gaussian(m, n, seed=m + n)
-    f, Aout = gpu_factor(A, nb, ib, tree)
-    F = otq.factor(A, nb, ib, tree)
+    BS = 3 if tree == tqr.PLASMA_TS else 1
+    f, Aout = gpu_factor(A, nb, ib, tree, BS)
+    F = otq.factor(A, nb, ib, tree, BS)
     compare(Aout, F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
     check_targets(f, A, Aout)
     f.free()
@@ -186,6 +188,23 @@ def test_caller_given_list():
     with pytest.raises(tqr.TqrError) as e:
         tqr.tqr_factor_list(tqr.colmajor(A), nb, ib, np.array(bad) - 1)
     assert e.value.code == tqr.TQR_ERR_INVALID_LIST
+    f.free()
+
+
+def test_ts_list_with_triangle_tile_is_rejected():
+    """TS kernels need the zeroed tile square: a BinaryTree list eliminates
+    rows that were pivots earlier in the column, so it is invalid with TS."""
+    p, q, nb, ib = 8, 2, 32, 8
+    el = np.array(otrees.binary_tree(p, q)) - 1
+    A = workloads.gaussian(p * nb, q * nb, seed=12)
+    with pytest.raises(tqr.TqrError) as e:
+        tqr.tqr_factor_list(tqr.colmajor(A), nb, ib, el, ts=True)
+    assert e.value.code == tqr.TQR_ERR_INVALID_LIST
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor_list(At, nb, ib, el, ts=False)     # the same list with TT kernels is fine
+    tqr.tqr_sync(f)
+    F = otq.factor(A, nb, ib, tqr.BINARY)
+    compare(tqr.to_numpy(At), F.A, np.abs(F.r()).max(), tol_for(A), "R and V")
     f.free()
 
 

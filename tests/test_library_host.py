@@ -94,11 +94,12 @@ def test_plasma_lists_match_oracle():
 @pytest.mark.parametrize("p,q,tree,BS", [(16, 4, tqr.GREEDY, 1), (15, 6, tqr.FIBONACCI, 1), (40, 17, tqr.PLASMA, 7),
                                          (64, 64, tqr.GREEDY, 1), (64, 8, tqr.FLAT_TS, 1), (33, 20, tqr.BINARY, 1),
                                          (9, 9, tqr.FLAT_TT, 1), (1, 1, tqr.GREEDY, 1), (7, 1, tqr.FLAT_TS, 1),
-                                         (15, 3, tqr.ASAP, 1), (21, 9, tqr.GRASAP, 3), (12, 12, tqr.GRASAP, 12)])
+                                         (15, 3, tqr.ASAP, 1), (21, 9, tqr.GRASAP, 3), (12, 12, tqr.GRASAP, 12),
+                                         (40, 17, tqr.PLASMA_TS, 7), (16, 16, tqr.PLASMA_TS, 3),
+                                         (9, 4, tqr.PLASMA_TS, 9), (13, 5, tqr.PLASMA_TS, 1)])
 def test_tasks_schedule_and_cp_match_oracle(p, q, tree, BS):
     el = otrees.elimination_list(p, q, tree, BS)
-    ts = tree == tqr.FLAT_TS
-    otasks = odag.expand(p, q, el, ts)
+    otasks = odag.expand(p, q, el, otrees.ts_flags(tree, BS, el))
     ofin, ocp = odag.simulate(otasks)
     tasks, fin = tqr.tqr_tasks(p, q, tree, BS)
     want = np.array([[KIND_MAP[k], i - 1, piv - 1 if piv else -1, kk - 1, j - 1 if j else -1]
@@ -119,6 +120,16 @@ def test_critical_paths_sweep_match_oracle():
             for tree in TREES:
                 el = otrees.elimination_list(p, q, tree)
                 assert tqr.tqr_critical_path(p, q, tree) == odag.critical_path(p, q, el, tree == tqr.FLAT_TS)
+
+
+def test_plasma_ts_critical_paths_match_oracle():
+    for p in range(1, 22):
+        for q in range(1, p + 1, 2):
+            for BS in range(1, p + 1, 3):
+                el = otrees.elimination_list(p, q, tqr.PLASMA_TS, BS)
+                want = odag.critical_path(p, q, el, otrees.ts_flags(tqr.PLASMA_TS, BS, el))
+                assert tqr.tqr_critical_path(p, q, tqr.PLASMA_TS, BS) == want, (p, q, BS)
+                assert lists_equal(p, q, tqr.PLASMA_TS, BS)
 
 
 def test_validator_agrees_with_oracle():

@@ -95,3 +95,15 @@ def test_noalloc_refuses_problems_beyond_its_scratch():
     assert L.tqr_factor_noalloc(a, 64 * 256, 32 * 256, 256, 32, eptr, elims.shape[0], 0, t, t, st,
                                 s) == tqr.TQR_ERR_TOO_LARGE
     assert "scratch" in tqr.tqr_strerror(tqr.TQR_ERR_TOO_LARGE)
+
+
+def test_noalloc_rejects_ts_on_triangle_tile():
+    """A BinaryTree list eliminates earlier pivots, whose tiles are triangles:
+    invalid with TS kernels, before anything is launched."""
+    p, q, nb, ib = 8, 2, 32, 8
+    A = tqr.colmajor(workloads.gaussian(p * nb, q * nb, seed=13))
+    elims = tqr.tqr_elimination_list(p, q, tqr.BINARY)
+    tau = torch.zeros(p * q * nb, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = tqr.tqr_factor_noalloc(A, nb, ib, elims, tau, tau.clone(), status, ts=True)
+    assert rc == tqr.TQR_ERR_INVALID_LIST
