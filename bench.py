@@ -425,17 +425,23 @@ def batched_main(args):
     work = [torch.empty_like(s.t()).t() for s in src]
     flops = float(sum(2.0 * n * n * (m - n / 3.0) for m, n in zip(ms, ns)))
 
-    def measure(cfgs):
+    def measure(cfgs, f32=False):
         nb, ib, tree, BS = (list(x) for x in zip(*cfgs))
         for w, s in zip(work, src):
             w.copy_(s)
-        b = tqr.tqr_factor_batched(work, nb, ib, tree, BS)
+        if f32:
+            b = tqr.tqr_factor_batched_f32(work, nb)
+        else:
+            b = tqr.tqr_factor_batched(work, nb, ib, tree, BS)
         tqr.tqr_batch_sync(b)
         stream = torch.cuda.Stream()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(stream):
             with torch.cuda.graph(graph, stream=stream):
-                tqr.tqr_factor_batched(work, nb, ib, tree, BS, stream=stream, reuse=b)
+                if f32:
+                    tqr.tqr_factor_batched_f32(work, nb, stream=stream, reuse=b)
+                else:
+                    tqr.tqr_factor_batched(work, nb, ib, tree, BS, stream=stream, reuse=b)
         for _ in range(args.warmup):
             for w, s in zip(work, src):
                 w.copy_(s)
@@ -458,19 +464,29 @@ def batched_main(args):
         b.free()
         return {"gflops": flops * args.steps / step_t / 1e9, "ms_per_step": 1e3 * step_t / args.steps,
                 "graph_ms": 1e3 * kern_t / args.steps, "kernel_gflops": flops * args.steps / kern_t / 1e9,
-                "status": rc, "tasks": info["n_tasks"]}
+                "status": rc, "tasks": info["n_tasks"], "one_column_matrices": info["n_fused"]}
 
     tuned_cfgs = [autotune.lookup(db, int(m), int(n)) for m, n in zip(ms, ns)]
     tuned = measure(tuned_cfgs)
     fixed_cfgs = [(min(64, int(n)), 16, tqr.GREEDY, 1) for n in ns]
     fixed = measure(fixed_cfgs)
+    # FP32: the same shapes, FlatTree-TS with one tile column, tile height tuned per class.
+    t32 = time.perf_counter()
+    db32 = autotune.tune(sample=args.tune_sample, f32=True)
+    t32 = time.perf_counter() - t32
+    src = [s.float() for s in src]
+    src = [s.t().contiguous().t() for s in src]
+    work = [torch.empty_like(s.t()).t() for s in src]
+    fp32 = measure([autotune.lookup(db32, int(m), int(n)) for m, n in zip(ms, ns)], f32=True)
+    fp32["tuning_seconds"] = t32
+    fp32["classes"] = [{k: c[k] for k in ("n", "m_lo", "m_hi", "nb", "gflops")} for c in db32["classes"]]
     line = {"metric": "batched tall-skinny QR GFLOP/s (FP64)", "value": tuned["gflops"], "unit": "GFLOP/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tuned["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "4096 FP64 matrices, m ~ U[512,16384], n in {32,64,128}, N(0,1); one "
                                    "persistent launch replayed from a CUDA graph; step = input restore + replay",
                        "count": BT_COUNT, "flops_per_step": flops},
-            "detail": {"tuned": tuned, "fixed_nb64_ib16_greedy": fixed,
+            "detail": {"tuned": tuned, "fixed_nb64_ib16_greedy": fixed, "fp32_tuned": fp32,
                        "speedup_tuned_vs_fixed": tuned["gflops"] / fixed["gflops"],
                        "tuning_seconds": t_tune,
                        "classes": [{k: c[k] for k in ("n", "m_lo", "m_hi", "nb", "ib", "tree", "BS", "gflops")}

@@ -244,11 +244,38 @@ typedef struct {
     int64_t n_edges;        /* dependency edges                             */
     int64_t max_critical_path; /* largest unit-weight critical path         */
     double flops;           /* sum of 2 n^2 (m - n/3)                       */
+    int32_t n_fused;        /* matrices run by the one-tile-column FlatTree-TS kernel */
+    int32_t f32;            /* 1 for a tqr_factor_batched_f32 batch         */
 } tqr_batch_info;
 
 int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
                        const int32_t* ib, const int32_t* tree, const int32_t* BS, void* stream,
                        tqr_batch** out);
+/* One tile column, FlatTree with TS kernels (q = 1).  A matrix with
+ * tree = TQR_FLAT_TS, n <= nb and n <= 128 is factored by a kernel that runs
+ * the whole chain GEQRT(1,1), TSQRT(2,1,1), ..., TSQRT(p,1,1) of one matrix in
+ * one CTA with R resident in shared memory (Proposition 2's flat tree; the
+ * batch supplies the parallelism), provided its shared memory fits (a tile of
+ * nb x (n rounded up to 32/64/128) entries plus the packed R): with FP64, n <= 64
+ * allows every nb <= 256 and n in 65..128 allows nb <= 128.  The results equal
+ * tqr_factor's for the same (nb, TQR_FLAT_TS) up to rounding.  Other matrices of
+ * the batch go to the task-graph executor in the same call; each kind is one
+ * launch (up to three column classes + the executor), all on `stream`.
+ *
+ * tqr_factor_batched_f32: the same for FP32 matrices (all arithmetic FP32);
+ * every matrix must satisfy the one-tile-column conditions above (with the
+ * FP32 shared-memory limit: every n <= 128 with nb <= 256), otherwise
+ * TQR_ERR_UNSUPPORTED.  Argument errors: -1 count, -2 A, -3 m, -4 n, -5 nb,
+ * -7 out.  Reuse and graph capture as for tqr_factor_batched.
+ *
+ * tqr_batch_tau: copies matrix c's tau values (p*q*nb entries each, of the
+ * batch's type, tile (i,k) reflector j at (k*p + i)*nb + j) into tau_ge
+ * (GEQRT) and tau_el (TSQRT/TTQRT), host or device buffers; waits for the
+ * batch's stream first. */
+int tqr_factor_batched_f32(int count, float* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
+                           void* stream, tqr_batch** out);
+int tqr_batch_tau(const tqr_batch* b, int c, void* tau_ge, void* tau_el);
+
 /* Waits for the batch's last launch; returns its device status. */
 int tqr_batch_sync(tqr_batch* b);
 int tqr_batch_get_info(const tqr_batch* b, tqr_batch_info* info);

@@ -17,15 +17,20 @@ import numpy as np
 
 from . import tqr
 
-DB_VERSION = 1
+DB_VERSION = 2
 M_BUCKETS = [(512, 1024), (1024, 2048), (2048, 4096), (4096, 8192), (8192, 16385)]
 N_CLASSES = [32, 64, 128]
 TREE_CANDIDATES = [(tqr.GREEDY, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1), (tqr.FLAT_TT, 1), (tqr.FLAT_TS, 1),
                    (tqr.PLASMA, 4), (tqr.PLASMA, 16), (tqr.ASAP, 1)]
 
 
+ONE_COLUMN_NB = (32, 64, 128, 256)
+
+
 def candidates(n, m_lo):
-    """(nb, ib, tree, BS) candidates for matrices with n columns."""
+    """(nb, ib, tree, BS) candidates for matrices with n columns: square tiles
+    nb <= n with every tree, plus FlatTree-TS with one tile column (nb >= n),
+    which runs each matrix in one CTA."""
     out = []
     for nb in (16, 32, 64, 128):
         if nb > n or nb > m_lo:
@@ -36,7 +41,15 @@ def candidates(n, m_lo):
             for tree, BS in TREE_CANDIDATES:
                 p_min = -(-m_lo // nb)
                 out.append((nb, ib, tree, min(BS, p_min)))
+    for nb in ONE_COLUMN_NB:
+        if nb >= n and (nb, 8, tqr.FLAT_TS, 1) not in out:
+            out.append((nb, 8, tqr.FLAT_TS, 1))
     return out
+
+
+def candidates_f32(n):
+    """Tile heights for FP32 batches (FlatTree-TS, one tile column)."""
+    return [(nb, nb, tqr.FLAT_TS, 1) for nb in ONE_COLUMN_NB if nb >= n]
 
 
 def sample_class(n, m_lo, m_hi, count, seed):
@@ -44,12 +57,13 @@ def sample_class(n, m_lo, m_hi, count, seed):
     return [int(m) for m in rng.integers(m_lo, m_hi, count)]
 
 
-def time_batch(ms, n, cfg, reps=2, seed=0):
+def time_batch(ms, n, cfg, reps=2, seed=0, f32=False):
     """Seconds for one batched launch of matrices (ms[i] x n) with config cfg."""
     import torch
     nb, ib, tree, BS = cfg
     g = torch.Generator(device="cuda").manual_seed(seed)
-    src = [torch.randn(n, m, generator=g, dtype=torch.float64, device="cuda").t() for m in ms]
+    dt = torch.float32 if f32 else torch.float64
+    src = [torch.randn(n, m, generator=g, dtype=dt, device="cuda").t() for m in ms]
     work = [torch.empty_like(s.t()).t() for s in src]
     b = None
     best = None
@@ -58,7 +72,10 @@ def time_batch(ms, n, cfg, reps=2, seed=0):
             w.copy_(s)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b = tqr.tqr_factor_batched(work, nb, ib, tree, BS, reuse=b)
+        if f32:
+            b = tqr.tqr_factor_batched_f32(work, nb, reuse=b)
+        else:
+            b = tqr.tqr_factor_batched(work, nb, ib, tree, BS, reuse=b)
         e1.record()
         tqr.tqr_batch_sync(b)
         t = e0.elapsed_time(e1) / 1e3
@@ -68,7 +85,7 @@ def time_batch(ms, n, cfg, reps=2, seed=0):
     return best
 
 
-def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, log=None):
+def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, log=None, f32=False):
     """Exhaustive search; returns the database (a dict)."""
     import torch
     classes = []
@@ -76,9 +93,9 @@ def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, lo
         for (lo, hi) in m_buckets:
             ms = sample_class(n, lo, hi, sample, seed + n + lo)
             results = []
-            for cfg in candidates(n, lo):
+            for cfg in (candidates_f32(n) if f32 else candidates(n, lo)):
                 try:
-                    t = time_batch(ms, n, cfg, reps=reps, seed=seed)
+                    t = time_batch(ms, n, cfg, reps=reps, seed=seed, f32=f32)
                 except tqr.TqrError:
                     continue
                 results.append((t, cfg))
@@ -91,7 +108,8 @@ def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, lo
             classes.append(rec)
             if log:
                 log(rec)
-    return {"version": DB_VERSION, "gpu": torch.cuda.get_device_name(0), "sample": sample, "classes": classes}
+    return {"version": DB_VERSION, "gpu": torch.cuda.get_device_name(0), "sample": sample, "classes": classes,
+            "dtype": "f32" if f32 else "f64"}
 
 
 def save(db, path):
@@ -117,6 +135,9 @@ def lookup(db, m, n):
         d = (dn, dm)
         if best is None or d < key:
             best, key = c, d
+    if best["tree"] == tqr.FLAT_TS and best["nb"] >= best["n"]:     # one tile column
+        nb = max(best["nb"], -(-n // 4) * 4)
+        return min(nb, 256), 8, tqr.FLAT_TS, 1
     nb = min(best["nb"], n)
     ib = min(best["ib"], nb)
     BS = best["BS"]

@@ -242,7 +242,8 @@ using namespace tqr;
 
 struct tqr_batch {
     int count = 0;
-    std::vector<double*> A;
+    bool f32 = false;          // FP32 matrices (tqr_factor_batched_f32)
+    std::vector<double*> A;    // identity of the matrices (FP32 pointers stored as is)
     std::vector<int64_t> m, n;
     std::vector<int32_t> nb, ib, tree, BS;
     DevGraphOwner dg;
@@ -255,7 +256,15 @@ struct tqr_batch {
     int64_t max_cp = 0;
     double flops = 0.0;
     cudaStream_t stream = nullptr;
+    // Matrices on the one-tile-column FlatTree-TS kernel, by column class 32 / 64 / 128.
+    struct Ts1Class {
+        Ts1Desc* d = nullptr;
+        int count = 0, hmax = 0;
+    } ts1[3];
+    int n_fused = 0;
+    bool has_exec = false;
     ~tqr_batch() {
+        for (auto& c : ts1) cudaFree(c.d);
         cudaFree(d_mats);
         cudaFree(tau_ge);
         cudaFree(tau_el);
@@ -784,6 +793,13 @@ int tqr_inject_fault(int kind) {
 }
 
 static int launch_batch(tqr_batch* b) {
+    if (cudaMemsetAsync(b->status, 0, sizeof(int32_t), b->stream) != cudaSuccess) return TQR_ERR_CUDA;
+    static const int kClass[3] = {32, 64, 128};
+    for (int k = 0; k < 3; ++k)
+        if (launch_ts1(b->ts1[k].d, b->ts1[k].count, kClass[k], b->ts1[k].hmax, b->f32, b->tau_ge, b->tau_el,
+                       b->status, b->stream) != cudaSuccess)
+            return TQR_ERR_CUDA;
+    if (!b->has_exec) return TQR_OK;
     ExecParams P{};
     P.tau_ge = b->tau_ge;
     P.tau_el = b->tau_el;
@@ -792,8 +808,30 @@ static int launch_batch(tqr_batch* b) {
     P.timeout_ns = timeout_ns(b->flops);
     P.nb = b->nb.empty() ? 0 : b->nb[0];
     P.ib = b->ib.empty() ? 0 : b->ib[0];
-    const cudaError_t e = launch_factor_exec(P, b->dg.d, b->st, b->G, b->smem, true, b->stream);
+    const cudaError_t e = launch_factor_exec(P, b->dg.d, b->st, b->G, b->smem, false, b->stream);
     return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+// Sorts the one-tile-column matrices of a batch into their column classes
+// (largest work first, so the hardware's in-order block dispatch balances
+// the SMs) and uploads their descriptors.
+static int build_ts1(tqr_batch* b, const std::vector<Ts1Desc>& fused) {
+    std::vector<Ts1Desc> cls[3];
+    for (const Ts1Desc& d : fused) {
+        const int k = ts1_ncol_class(d.n) == 32 ? 0 : (ts1_ncol_class(d.n) == 64 ? 1 : 2);
+        cls[k].push_back(d);
+        b->ts1[k].hmax = std::max(b->ts1[k].hmax, d.h);
+        b->max_cp = std::max<int64_t>(b->max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
+    }
+    for (int k = 0; k < 3; ++k) {
+        std::stable_sort(cls[k].begin(), cls[k].end(), [](const Ts1Desc& x, const Ts1Desc& y) {
+            return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
+        });
+        b->ts1[k].count = static_cast<int>(cls[k].size());
+        if (!cls[k].empty() && upload(&b->ts1[k].d, cls[k]) != cudaSuccess) return TQR_ERR_NOMEM;
+    }
+    b->n_fused = static_cast<int>(fused.size());
+    return TQR_OK;
 }
 
 int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
@@ -840,8 +878,18 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
         const int W = strip_width(b->G);
         Graph all;
         std::vector<MatDesc> mats(count);
+        std::vector<Ts1Desc> fused;
         int64_t tau_off = 0;
         for (int c = 0; c < count; ++c) {
+            if (tree[c] == TQR_FLAT_TS && ts1_supported(m[c], n[c], nb[c], sizeof(double))) {
+                const int64_t p = (m[c] + nb[c] - 1) / nb[c];
+                fused.push_back(Ts1Desc{A[c], m[c], static_cast<int32_t>(n[c]), nb[c], tau_off});
+                mats[c] = MatDesc{A[c], m[c], m[c], n[c], nb[c], ib[c], static_cast<int>(p), 1, tau_off};
+                b->flops += lapack_flops(m[c], n[c]);
+                tau_off += p * nb[c];
+                continue;
+            }
+            b->has_exec = true;
             const int t = tree[c] == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree[c];
             const int bs = uses_bs(t) ? BS[c] : 0;
             std::shared_ptr<HostPlan> H;
@@ -866,13 +914,14 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
             mats[c] = MatDesc{A[c], m[c], m[c], n[c], nb[c], ib[c], H->p, H->q, tau_off};
             tau_off += static_cast<int64_t>(H->p) * H->q * nb[c];
         }
-        if (upload_graph(all, b->dg) != cudaSuccess) return TQR_ERR_NOMEM;
+        if (b->has_exec && upload_graph(all, b->dg) != cudaSuccess) return TQR_ERR_NOMEM;
         if (upload(&b->d_mats, mats) != cudaSuccess) return TQR_ERR_NOMEM;
         if (cudaMalloc(&b->tau_ge, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess ||
-            alloc_state(b->st, b->dg.d.ntasks, b->status) != cudaSuccess)
+            (b->has_exec && alloc_state(b->st, b->dg.d.ntasks, b->status) != cudaSuccess))
             return TQR_ERR_NOMEM;
+        if (build_ts1(b, fused) != TQR_OK) return TQR_ERR_NOMEM;
         b->stream = static_cast<cudaStream_t>(stream);
         const int rc = launch_batch(b);
         if (rc != TQR_OK) return rc;
@@ -883,6 +932,84 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
     } catch (...) {
         return TQR_ERR_INTERNAL;
     }
+}
+
+int tqr_factor_batched_f32(int count, float* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
+                           void* stream, tqr_batch** out) {
+    try {
+        if (count < 1 || count > (1 << 23)) return -1;
+        if (!A) return -2;
+        if (!m) return -3;
+        if (!n) return -4;
+        if (!nb) return -5;
+        if (!out) return -7;
+        for (int c = 0; c < count; ++c) {
+            if (!A[c]) return -2;
+            if (m[c] < 1) return -3;
+            if (n[c] < 1 || n[c] > m[c]) return -4;
+            if (nb[c] < 8 || nb[c] > 256 || nb[c] % 4 != 0 || (m[c] + nb[c] - 1) / nb[c] > 65535) return -5;
+            if (!ts1_supported(m[c], n[c], nb[c], sizeof(float))) return TQR_ERR_UNSUPPORTED;
+        }
+        const std::vector<int32_t> ones(count, 1), flat(count, TQR_FLAT_TS);
+        std::vector<double*> ids(count);
+        for (int c = 0; c < count; ++c) ids[c] = reinterpret_cast<double*>(A[c]);
+        tqr_batch* b = *out;
+        if (b && b->f32 && b->same(count, ids.data(), m, n, nb, nb, flat.data(), ones.data())) {
+            b->stream = static_cast<cudaStream_t>(stream);
+            return launch_batch(b);
+        }
+        auto nbh = std::make_unique<tqr_batch>();
+        b = nbh.get();
+        b->count = count;
+        b->f32 = true;
+        b->A = ids;
+        b->m.assign(m, m + count);
+        b->n.assign(n, n + count);
+        b->nb.assign(nb, nb + count);
+        b->ib.assign(nb, nb + count);
+        b->tree = flat;
+        b->BS = ones;
+        std::vector<Ts1Desc> fused(count);
+        int64_t tau_off = 0;
+        for (int c = 0; c < count; ++c) {
+            fused[c] = Ts1Desc{A[c], m[c], static_cast<int32_t>(n[c]), nb[c], tau_off};
+            tau_off += (m[c] + nb[c] - 1) / nb[c] * nb[c];
+            b->flops += lapack_flops(m[c], n[c]);
+        }
+        if (cudaMalloc(&b->tau_ge, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess)
+            return TQR_ERR_NOMEM;
+        if (build_ts1(b, fused) != TQR_OK) return TQR_ERR_NOMEM;
+        b->stream = static_cast<cudaStream_t>(stream);
+        const int rc = launch_batch(b);
+        if (rc != TQR_OK) return rc;
+        *out = nbh.release();
+        return TQR_OK;
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_batch_tau(const tqr_batch* b, int c, void* tau_ge, void* tau_el) {
+    if (!b) return -1;
+    if (c < 0 || c >= b->count) return -2;
+    if (!tau_ge) return -3;
+    if (!tau_el) return -4;
+    const size_t esz = b->f32 ? sizeof(float) : sizeof(double);
+    int64_t off = 0;
+    for (int x = 0; x < c; ++x)
+        off += (b->m[x] + b->nb[x] - 1) / b->nb[x] * ((b->n[x] + b->nb[x] - 1) / b->nb[x]) * b->nb[x];
+    const int64_t len = (b->m[c] + b->nb[c] - 1) / b->nb[c] * ((b->n[c] + b->nb[c] - 1) / b->nb[c]) * b->nb[c];
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TQR_ERR_CUDA;
+    const char* ge = reinterpret_cast<const char*>(b->tau_ge) + off * esz;
+    const char* el = reinterpret_cast<const char*>(b->tau_el) + off * esz;
+    if (cudaMemcpy(tau_ge, ge, len * esz, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(tau_el, el, len * esz, cudaMemcpyDefault) != cudaSuccess)
+        return TQR_ERR_CUDA;
+    return TQR_OK;
 }
 
 int tqr_batch_sync(tqr_batch* b) {
@@ -902,6 +1029,8 @@ int tqr_batch_get_info(const tqr_batch* b, tqr_batch_info* info) {
     info->n_edges = b->dg.d.nedges;
     info->max_critical_path = b->max_cp;
     info->flops = b->flops;
+    info->n_fused = b->n_fused;
+    info->f32 = b->f32 ? 1 : 0;
     return TQR_OK;
 }
 

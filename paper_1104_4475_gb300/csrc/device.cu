@@ -232,58 +232,84 @@ __device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int i
 //   GE: alpha = Vs[j, jj], x = Vs[j+1.., jj]   (GEQRT)
 //   TT: alpha = Ct[jj, jj], x = Vs[0..j, jj]   (TTQRT)
 //   TS: alpha = Ct[jj, jj], x = Vs[0..nb-1, jj] (TSQRT)
-// Warp 0 forms each reflector; the 8 warps then update the remaining panel
-// columns, one column per warp at a time.
+// Warp 0 forms reflector 0.  Then, for each reflector jj, warp 0 applies it to
+// column jj+1 and at once forms reflector jj+1 from that column, while warps
+// 1..7 apply reflector jj to columns jj+2.. of the block: one block barrier
+// per reflector, and reflector generation overlaps the other columns' updates.
 // ----------------------------------------------------------------------------
 template <int MODE>
+__device__ __forceinline__ void fb_range(int j, int nb, int* rlo, int* rhi) {
+    *rlo = (MODE == GE) ? j + 1 : 0;
+    *rhi = (MODE == TT) ? j + 1 : nb;
+}
+
+// Warp-level: forms reflector jj of the block from column jj of Vs (and its
+// alpha), writes beta over alpha, tau into S.taus[jj], and v in place.
+template <int MODE>
+__device__ void fb_form(const Smem& S, int nb, int j0, int jj, int lane, int32_t* status) {
+    const int j = j0 + jj;
+    double* v = S.Vs + jj * nb;
+    int rlo, rhi;
+    fb_range<MODE>(j, nb, &rlo, &rhi);
+    double sig = 0.0;
+    for (int r = rlo + lane; r < rhi; r += 32) sig = fma(v[r], v[r], sig);
+    sig = warp_sum(sig);
+    double scale = 0.0;
+    if (lane == 0) {
+        double* ap = (MODE == GE) ? &v[j] : &S.Ct[jj + jj * S.ldt];
+        const double alpha = *ap;
+        double tau = 0.0;
+        if (sig != 0.0 || !isfinite(sig)) {
+            const double nrm = sqrt(fma(alpha, alpha, sig));
+            if (!isfinite(nrm)) set_status(status, TQR_ERR_NONFINITE);
+            const double beta = alpha >= 0.0 ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+            *ap = beta;
+        }                                   // else x is zero: identity reflector, zero tail
+        S.taus[jj] = tau;
+    }
+    scale = __shfl_sync(kFull, scale, 0);
+    for (int r = rlo + lane; r < rhi; r += 32) v[r] *= scale;
+}
+
+// Warp-level: applies reflector jj (v in column jj, tau) to column cc of the block.
+template <int MODE>
+__device__ __forceinline__ void fb_apply(const Smem& S, int nb, int j0, int jj, int cc, double tau, int lane) {
+    const int j = j0 + jj;
+    const double* v = S.Vs + jj * nb;
+    double* u = S.Vs + cc * nb;
+    int rlo, rhi;
+    fb_range<MODE>(j, nb, &rlo, &rhi);
+    double acc = 0.0;
+    for (int r = rlo + lane; r < rhi; r += 32) acc = fma(v[r], u[r], acc);
+    if (lane == 0) acc += (MODE == GE) ? u[j] : S.Ct[jj + cc * S.ldt];
+    acc = warp_sum(acc);
+    const double w = tau * acc;
+    if (lane == 0) {
+        if (MODE == GE) u[j] -= w;
+        else S.Ct[jj + cc * S.ldt] -= w;
+    }
+    for (int r = rlo + lane; r < rhi; r += 32) u[r] = fma(-v[r], w, u[r]);
+}
+
+template <int MODE>
 __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* status) {
-    __shared__ double s_scale;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    constexpr int kWarps = kThreads / 32;
+    if (warp == 0) fb_form<MODE>(S, nb, j0, 0, lane, status);
+    __syncthreads();
     for (int jj = 0; jj < ib; ++jj) {
-        const int j = j0 + jj;
-        double* v = S.Vs + jj * nb;
-        const int rlo = (MODE == GE) ? j + 1 : 0;
-        const int rhi = (MODE == TT) ? j + 1 : nb;
-        if (warp == 0) {
-            double sig = 0.0;
-            for (int r = rlo + lane; r < rhi; r += 32) sig = fma(v[r], v[r], sig);
-            sig = warp_sum(sig);
-            if (lane == 0) {
-                double* ap = (MODE == GE) ? &v[j] : &S.Ct[jj + jj * S.ldt];
-                const double alpha = *ap;
-                double tau = 0.0, scale = 0.0;
-                if (sig != 0.0 || !isfinite(sig)) {
-                    const double nrm = sqrt(fma(alpha, alpha, sig));
-                    if (!isfinite(nrm)) set_status(status, TQR_ERR_NONFINITE);
-                    const double beta = alpha >= 0.0 ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scale = 1.0 / (alpha - beta);
-                    *ap = beta;
-                } else {
-                    scale = 0.0;   // x is zero: identity reflector, zero tail
-                }
-                S.taus[jj] = tau;
-                s_scale = scale;
-            }
-            __syncwarp();
-            const double sc = s_scale;
-            for (int r = rlo + lane; r < rhi; r += 32) v[r] *= sc;
-        }
-        __syncthreads();
         const double tau = S.taus[jj];
-        for (int cc = jj + 1 + warp; cc < ib; cc += kThreads / 32) {
-            double* u = S.Vs + cc * nb;
-            double acc = 0.0;
-            for (int r = rlo + lane; r < rhi; r += 32) acc = fma(v[r], u[r], acc);
-            if (lane == 0) acc += (MODE == GE) ? u[j] : S.Ct[jj + cc * S.ldt];
-            acc = warp_sum(acc);
-            const double w = tau * acc;
-            if (lane == 0) {
-                if (MODE == GE) u[j] -= w;
-                else S.Ct[jj + cc * S.ldt] -= w;
+        if (warp == 0) {
+            if (jj + 1 < ib) {
+                fb_apply<MODE>(S, nb, j0, jj, jj + 1, tau, lane);
+                __syncwarp();
+                fb_form<MODE>(S, nb, j0, jj + 1, lane, status);
             }
-            for (int r = rlo + lane; r < rhi; r += 32) u[r] = fma(-v[r], w, u[r]);
+        } else {
+            for (int cc = jj + 1 + warp; cc < ib; cc += kWarps - 1) fb_apply<MODE>(S, nb, j0, jj, cc, tau, lane);
         }
         __syncthreads();
     }

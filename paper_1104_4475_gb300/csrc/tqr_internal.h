@@ -130,6 +130,20 @@ int fp64_smem_bytes(int nb, int ib, int G);
 int device_sm_count();
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,
                                int smem, bool reset_status, cudaStream_t s);
+// Batched FlatTree-TS for one tile column (q = 1): one CTA per matrix, R in
+// shared memory.  A matrix of n <= 128 columns with n <= nb runs there when its
+// shared memory (tile of nb rows, packed R) fits; ncol_class is 32, 64 or 128.
+struct Ts1Desc {
+    void* A;            // column-major, leading dimension m (double or float)
+    int64_t m;
+    int32_t n, h;       // columns, tile height nb
+    int64_t tau_off;    // offset of the matrix's tau block (p * nb entries)
+};
+int ts1_ncol_class(int64_t n);
+int ts1_smem_bytes(int ncol_class, int hmax, int elem_size);
+bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size);
+cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int hmax, bool f32, void* tau_ge,
+                       void* tau_el, int32_t* status, cudaStream_t s);
 // T factors of the listed panel tasks (kind, i, k triplets on the device).
 cudaError_t launch_form_t(const ExecParams& P, const int32_t* panels, int npanels,
                           double* T_ge, double* T_el, cudaStream_t s);

@@ -29,6 +29,8 @@ TQR_ERR_NONFINITE = -102
 TQR_ERR_CUDA = -103
 TQR_ERR_NOMEM = -104
 TQR_ERR_CAPACITY = -105
+TQR_ERR_INTERNAL = -106
+TQR_ERR_UNSUPPORTED = -107
 TQR_ERR_TOO_LARGE = -108
 
 
@@ -50,7 +52,8 @@ class tqr_lstsq_info(ctypes.Structure):
 
 class tqr_batch_info(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("strip", ctypes.c_int32), ("n_tasks", ctypes.c_int64),
-                ("n_edges", ctypes.c_int64), ("max_critical_path", ctypes.c_int64), ("flops", ctypes.c_double)]
+                ("n_edges", ctypes.c_int64), ("max_critical_path", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("n_fused", ctypes.c_int32), ("f32", ctypes.c_int32)]
 
 
 class tqr_info(ctypes.Structure):
@@ -94,6 +97,8 @@ def lib():
             "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
                                    ctypes.POINTER(vp)],
             "tqr_batch_sync": [vp],
+            "tqr_factor_batched_f32": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, vp, ctypes.POINTER(vp)],
+            "tqr_batch_tau": [vp, i32, vp, vp],
             "tqr_mlp_param_count": [i32],
             "tqr_mlp_forward": [vp, i32, vp, i32, vp, vp],
             "tqr_mlp_loss_grad": [vp, i32, vp, vp, i32, vp, vp, vp, vp],
@@ -136,10 +141,11 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def _colmajor_ptr(t, what):
+def _colmajor_ptr(t, what, dtype=None):
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
-        raise TypeError("%s must be a 2-D float64 CUDA tensor" % what)
+    dtype = torch.float64 if dtype is None else dtype
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or t.dim() != 2:
+        raise TypeError("%s must be a 2-D %s CUDA tensor" % (what, str(dtype).replace("torch.", "")))
     m = t.shape[0]
     if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) < m):
         raise ValueError("%s must be column-major (stride (1, ld) with ld >= rows)" % what)
@@ -320,6 +326,45 @@ def tqr_factor_batched(As, nb, ib, tree, BS=1, stream=None, reuse=None):
     if reuse is not None and h.value == reuse.ptr:
         return reuse
     return Batch(h.value, (ptrs, m, n, arrs), list(As))
+
+
+def tqr_factor_batched_f32(As, nb, stream=None, reuse=None):
+    """FP32 batch (column-major float32 CUDA tensors), FlatTree-TS with one
+    tile column per matrix (n <= nb, n <= 128); nb is a scalar or one value
+    per matrix."""
+    import torch
+    count = len(As)
+    ptrs = (ctypes.c_void_p * count)()
+    m = np.zeros(count, dtype=np.int64)
+    n = np.zeros(count, dtype=np.int64)
+    for c, A in enumerate(As):
+        p, ld = _colmajor_ptr(A, "A[%d]" % c, torch.float32)
+        if ld != A.shape[0]:
+            raise ValueError("A[%d] must have leading dimension m" % c)
+        ptrs[c] = p.value
+        m[c], n[c] = A.shape
+    nbs = _per_matrix(nb, count, np.int32)
+    h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
+    rc = lib().tqr_factor_batched_f32(count, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)),
+                                      m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      nbs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream(stream),
+                                      ctypes.byref(h))
+    _check(rc, "tqr_factor_batched_f32")
+    if reuse is not None and h.value == reuse.ptr:
+        return reuse
+    return Batch(h.value, (ptrs, m, n, nbs), list(As))
+
+
+def tqr_batch_tau(b, c, m, n, nb, f32=False):
+    """(tau_ge, tau_el) of matrix c of a batch as host arrays of p*q*nb."""
+    p, q = -(-m // nb), -(-n // nb)
+    dt = np.float32 if f32 else np.float64
+    tg = np.zeros(p * q * nb, dtype=dt)
+    te = np.zeros(p * q * nb, dtype=dt)
+    _check(lib().tqr_batch_tau(ctypes.c_void_p(b.ptr), int(c), tg.ctypes.data_as(ctypes.c_void_p),
+                               te.ctypes.data_as(ctypes.c_void_p)), "tqr_batch_tau")
+    return tg, te
 
 
 def tqr_batch_sync(b, raise_on_error=True):

@@ -81,3 +81,111 @@ def test_batched_relaunch_and_cuda_graph():
         for a, e in zip(As, eager):
             assert np.array_equal(tqr.to_numpy(a), e)
     b.free()
+
+
+# --------------------------------------------- one tile column, FlatTree-TS
+from oracle import FLAT_TS as O_FLAT_TS
+from oracle import kernels as oK
+
+ONE_COLUMN = [(300, 32, 64), (1000, 64, 64), (517, 100, 128), (64, 64, 64), (70, 48, 64), (500, 1, 32),
+              (1200, 128, 128), (40, 32, 256), (2000, 64, 256), (777, 33, 64), (129, 96, 128)]
+
+
+def test_one_column_flat_ts_matches_oracle_with_tau():
+    """FlatTree-TS with n <= nb runs whole matrices in one CTA each; R, V
+    and every tau equal the oracle's (Proposition 2's chain GEQRT, TSQRT, ...)."""
+    mats = [workloads.gaussian(m, n, seed=50 + c) for c, (m, n, nb) in enumerate(ONE_COLUMN)]
+    nbs = [nb for (_, _, nb) in ONE_COLUMN]
+    As = [tqr.colmajor(A) for A in mats]
+    b = tqr.tqr_factor_batched(As, nbs, 8, tqr.FLAT_TS, 1)
+    assert tqr.tqr_batch_sync(b) == 0
+    info = b.info()
+    assert info["n_fused"] == len(mats) and info["n_tasks"] == 0
+    for c, (A, At, nb) in enumerate(zip(mats, As, nbs)):
+        m, n = A.shape
+        F = otq.factor(A, nb, 8, O_FLAT_TS)
+        tol = max(1e-13, 8 * np.linalg.cond(A) * m * U)
+        scale = np.abs(F.r()).max()
+        assert np.abs(tqr.to_numpy(At) - F.A).max() / scale <= tol, (m, n, nb)
+        tg, te = tqr.tqr_batch_tau(b, c, m, n, nb)
+        p = -(-m // nb)
+        assert np.abs(tg[:nb] - oK.tau_of(F.Tge[0, 0])).max() <= tol
+        for i in range(1, p):
+            assert np.abs(te[i * nb:(i + 1) * nb] - oK.tau_of(F.Tel[i, 0])).max() <= tol, (m, n, nb, i)
+    b.free()
+
+
+def test_one_column_mixed_with_executor_and_graph():
+    """A batch mixing one-column FlatTree-TS matrices with executor trees;
+    a CUDA-graph relaunch reproduces the eager result bit for bit."""
+    cfgs = [(800, 64, 64, tqr.FLAT_TS), (900, 96, 32, tqr.GREEDY), (600, 32, 128, tqr.FLAT_TS),
+            (1000, 128, 64, tqr.FLAT_TS), (700, 64, 32, tqr.BINARY), (300, 200, 256, tqr.FLAT_TS)]
+    mats = [workloads.gaussian(m, n, seed=70 + c) for c, (m, n, nb, t) in enumerate(cfgs)]
+    src = [tqr.colmajor(A) for A in mats]
+    As = [torch.empty_like(s.t()).t() for s in src]
+    for a, s in zip(As, src):
+        a.copy_(s)
+    nbs, trs = [c[2] for c in cfgs], [c[3] for c in cfgs]
+    b = tqr.tqr_factor_batched(As, nbs, 8, trs, 1)
+    assert tqr.tqr_batch_sync(b) == 0
+    assert b.info()["n_fused"] == 2                   # 800x64/64, 600x32/128 (1000x128 has n > nb; 300x200 n > 128)
+    eager = [tqr.to_numpy(a) for a in As]
+    for A, e, (m, n, nb, t) in zip(mats, eager, cfgs):
+        F = otq.factor(A, nb, 8, t)
+        tol = max(1e-13, 8 * np.linalg.cond(A) * m * U)
+        assert np.abs(e - F.A).max() / np.abs(F.r()).max() <= tol, (m, n, nb, t)
+    for a, s in zip(As, src):
+        a.copy_(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            b2 = tqr.tqr_factor_batched(As, nbs, 8, trs, 1, stream=stream, reuse=b)
+    assert b2 is b
+    for a, s in zip(As, src):
+        a.copy_(s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert tqr.tqr_batch_sync(b) == 0
+    for a, e in zip(As, eager):
+        assert np.array_equal(tqr.to_numpy(a), e)
+    b.free()
+
+
+U32 = 2.0 ** -24
+
+
+def test_fp32_batch_matches_oracle():
+    """FP32 one-column batch: R and V against the FP64 oracle within the
+    FP32 perturbation bound 8 kappa m u32, and R^T R = A^T A to m n u32."""
+    shapes = ONE_COLUMN + [(3000, 128, 256), (16384, 32, 256)]
+    mats = [workloads.gaussian(m, n, seed=90 + c) for c, (m, n, nb) in enumerate(shapes)]
+    As = [torch.tensor(np.asfortranarray(A, dtype=np.float32).T, device="cuda").t() for A in mats]
+    nbs = [nb for (_, _, nb) in shapes]
+    b = tqr.tqr_factor_batched_f32(As, nbs)
+    assert tqr.tqr_batch_sync(b) == 0
+    info = b.info()
+    assert info["f32"] == 1 and info["n_fused"] == len(mats)
+    for c, (A, At, nb) in enumerate(zip(mats, As, nbs)):
+        m, n = A.shape
+        A32 = A.astype(np.float32).astype(np.float64)
+        F = otq.factor(A32, nb, 8, O_FLAT_TS)
+        got = At.t().cpu().numpy().T.astype(np.float64)
+        tol = 8 * np.linalg.cond(A32) * m * U32
+        assert np.abs(got - F.A).max() / np.abs(F.r()).max() <= tol, (m, n, nb)
+        R = np.triu(got[:n, :n])
+        assert np.linalg.norm(R.T @ R - A32.T @ A32) / np.linalg.norm(A32) ** 2 <= m * n * U32
+        tg, te = tqr.tqr_batch_tau(b, c, m, n, nb, f32=True)
+        assert np.abs(tg[:nb] - oK.tau_of(F.Tge[0, 0])).max() <= tol
+    b.free()
+
+
+def test_fp32_batch_rejects_unsupported():
+    A = torch.zeros(300, 200, dtype=torch.float32, device="cuda").t().contiguous().t()
+    with pytest.raises(tqr.TqrError) as e:
+        tqr.tqr_factor_batched_f32([A], 256)
+    assert e.value.code == tqr.TQR_ERR_UNSUPPORTED
+    B = torch.zeros(300, 64, dtype=torch.float32, device="cuda").t().contiguous().t()
+    with pytest.raises(tqr.TqrError):
+        tqr.tqr_factor_batched_f32([B], 32)               # n > nb
