@@ -254,17 +254,17 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
 /* One tile column, FlatTree with TS kernels (q = 1).  A matrix with
  * tree = TQR_FLAT_TS, n <= nb and n <= 128 is factored by a kernel that runs
  * the whole chain GEQRT(1,1), TSQRT(2,1,1), ..., TSQRT(p,1,1) of one matrix in
- * one CTA with R resident in shared memory (Proposition 2's flat tree; the
- * batch supplies the parallelism), provided its shared memory fits (a tile of
- * nb x (n rounded up to 32/64/128) entries plus the packed R): with FP64, n <= 64
- * allows every nb <= 256 and n in 65..128 allows nb <= 128.  The results equal
+ * one CTA with the tile in registers and R resident in shared memory
+ * (Proposition 2's flat tree; the batch supplies the parallelism), provided nb
+ * is 64, 128 or 256 and at least n rounded up to 32 / 64 / 128; with FP64,
+ * n in 65..128 needs nb = 128.  The results equal
  * tqr_factor's for the same (nb, TQR_FLAT_TS) up to rounding.  Other matrices of
  * the batch go to the task-graph executor in the same call; each kind is one
  * launch (up to three column classes + the executor), all on `stream`.
  *
  * tqr_factor_batched_f32: the same for FP32 matrices (all arithmetic FP32);
- * every matrix must satisfy the one-tile-column conditions above (with the
- * FP32 shared-memory limit: every n <= 128 with nb <= 256), otherwise
+ * every matrix must satisfy the one-tile-column conditions above (FP32 also
+ * allows nb = 256 with n in 65..128), otherwise
  * TQR_ERR_UNSUPPORTED.  Argument errors: -1 count, -2 A, -3 m, -4 n, -5 nb,
  * -7 out.  Reuse and graph capture as for tqr_factor_batched.
  *

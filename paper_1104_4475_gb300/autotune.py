@@ -24,7 +24,7 @@ TREE_CANDIDATES = [(tqr.GREEDY, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1), (tqr.FL
                    (tqr.PLASMA, 4), (tqr.PLASMA, 16), (tqr.ASAP, 1)]
 
 
-ONE_COLUMN_NB = (32, 64, 128, 256)
+ONE_COLUMN_NB = (64, 128, 256)
 
 
 def candidates(n, m_lo):
@@ -85,8 +85,15 @@ def time_batch(ms, n, cfg, reps=2, seed=0, f32=False):
     return best
 
 
-def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, log=None, f32=False):
-    """Exhaustive search; returns the database (a dict)."""
+def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, log=None, f32=False, full=304,
+         shortlist=3):
+    """Exhaustive search in two stages; returns the database (a dict).
+
+    Stage 1 times every candidate on `sample` matrices of the class.  A small
+    sample favours configurations that spread one matrix over many SMs, so
+    stage 2 re-times the `shortlist` best of stage 1 and every one-column
+    candidate (one CTA per matrix) on `full` matrices (the sample repeated),
+    enough to fill the GPU, and keeps the fastest per matrix."""
     import torch
     classes = []
     for n in n_classes:
@@ -100,6 +107,18 @@ def tune(n_classes=N_CLASSES, m_buckets=M_BUCKETS, sample=32, reps=2, seed=7, lo
                     continue
                 results.append((t, cfg))
             results.sort()
+            if full and full > sample:
+                big = [ms[i % len(ms)] for i in range(full)]
+                short = [cfg for _, cfg in results[:shortlist]]
+                short += [cfg for _, cfg in results if cfg[2] == tqr.FLAT_TS and cfg[0] >= n and cfg not in short]
+                results = []
+                for cfg in short:
+                    try:
+                        t = time_batch(big, n, cfg, reps=1, seed=seed, f32=f32) * len(ms) / len(big)
+                    except tqr.TqrError:
+                        continue
+                    results.append((t, cfg))
+                results.sort()
             t, (nb, ib, tree, BS) = results[0]
             flops = sum(2.0 * n * n * (m - n / 3.0) for m in ms)
             rec = {"n": n, "m_lo": lo, "m_hi": hi, "nb": nb, "ib": ib, "tree": tree, "BS": BS, "seconds": t,

@@ -2,7 +2,9 @@
 
 Every translation unit is compiled for sm_103a only, in parallel; objects go to
 ``_build/`` inside the package and the library to ``libtqr.so`` beside this
-file.  A source newer than the library triggers a rebuild.
+file.  ``exec_inst.cu`` is compiled once per executor instantiation (G, PREC)
+so that the nine persistent-executor kernels compile in parallel.  A source
+newer than the library triggers a rebuild.
 """
 
 import concurrent.futures
@@ -29,8 +31,12 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
+EXEC_INST = "exec_inst.cu"
+EXEC_PAIRS = [(g, p) for g in (4, 8, 16) for p in (0, 1, 2)]
+
+
 def _headers():
-    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs.append(os.path.join(os.path.dirname(HERE), "include", "tqr.h"))
     return hs
 
@@ -50,6 +56,12 @@ def build(force=False, verbose=False, extra_flags=()):
     os.makedirs(BUILD, exist_ok=True)
     jobs = []
     for src in sources():
+        if os.path.basename(src) == EXEC_INST:
+            for g, p in EXEC_PAIRS:
+                obj = os.path.join(BUILD, "exec_g%d_p%d.o" % (g, p))
+                cmd = [nvcc, "-c", src, "-o", obj, "-DTQR_G=%d" % g, "-DTQR_PREC=%d" % p] + ARCH + FLAGS + list(extra_flags)
+                jobs.append((cmd, obj))
+            continue
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [nvcc, "-c", src, "-o", obj] + ARCH + FLAGS + list(extra_flags)
         jobs.append((cmd, obj))

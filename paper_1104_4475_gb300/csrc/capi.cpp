@@ -256,11 +256,12 @@ struct tqr_batch {
     int64_t max_cp = 0;
     double flops = 0.0;
     cudaStream_t stream = nullptr;
-    // Matrices on the one-tile-column FlatTree-TS kernel, by column class 32 / 64 / 128.
+    // Matrices on the one-tile-column FlatTree-TS kernel, by (column class 32 / 64 / 128,
+    // tile height 64 / 128 / 256).
     struct Ts1Class {
         Ts1Desc* d = nullptr;
-        int count = 0, hmax = 0;
-    } ts1[3];
+        int count = 0, ncol = 0, h = 0;
+    } ts1[9];
     int n_fused = 0;
     bool has_exec = false;
     ~tqr_batch() {
@@ -794,10 +795,8 @@ int tqr_inject_fault(int kind) {
 
 static int launch_batch(tqr_batch* b) {
     if (cudaMemsetAsync(b->status, 0, sizeof(int32_t), b->stream) != cudaSuccess) return TQR_ERR_CUDA;
-    static const int kClass[3] = {32, 64, 128};
-    for (int k = 0; k < 3; ++k)
-        if (launch_ts1(b->ts1[k].d, b->ts1[k].count, kClass[k], b->ts1[k].hmax, b->f32, b->tau_ge, b->tau_el,
-                       b->status, b->stream) != cudaSuccess)
+    for (const auto& k : b->ts1)
+        if (launch_ts1(k.d, k.count, k.ncol, k.h, b->f32, b->tau_ge, b->tau_el, b->status, b->stream) != cudaSuccess)
             return TQR_ERR_CUDA;
     if (!b->has_exec) return TQR_OK;
     ExecParams P{};
@@ -816,14 +815,16 @@ static int launch_batch(tqr_batch* b) {
 // (largest work first, so the hardware's in-order block dispatch balances
 // the SMs) and uploads their descriptors.
 static int build_ts1(tqr_batch* b, const std::vector<Ts1Desc>& fused) {
-    std::vector<Ts1Desc> cls[3];
+    std::vector<Ts1Desc> cls[9];
     for (const Ts1Desc& d : fused) {
-        const int k = ts1_ncol_class(d.n) == 32 ? 0 : (ts1_ncol_class(d.n) == 64 ? 1 : 2);
+        const int nc = ts1_ncol_class(d.n);
+        const int k = (nc == 32 ? 0 : (nc == 64 ? 1 : 2)) * 3 + (d.h == 64 ? 0 : (d.h == 128 ? 1 : 2));
         cls[k].push_back(d);
-        b->ts1[k].hmax = std::max(b->ts1[k].hmax, d.h);
+        b->ts1[k].ncol = nc;
+        b->ts1[k].h = d.h;
         b->max_cp = std::max<int64_t>(b->max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 9; ++k) {
         std::stable_sort(cls[k].begin(), cls[k].end(), [](const Ts1Desc& x, const Ts1Desc& y) {
             return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
         });

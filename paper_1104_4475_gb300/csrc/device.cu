@@ -1,879 +1,11 @@
-// Device side of libtqr: the persistent DAG executor and the six FP64 tile
-// kernels of tiled Householder QR ("Tiled QR factorization algorithms",
-// Bouwmeester, Jacquelin, Langou, Robert, 2011; kernels of Section 2.1,
-// execution scheme of Section 2.3).
-//
-// Design (sm_103a, FP64):
-//  * One persistent launch runs a whole task graph.  Each CTA pops a task id
-//    from a global ready queue, runs the task with all 256 threads, then
-//    decrements its successors' dependency counters and pushes the ones that
-//    reach zero.  Every wait is bounded by a %globaltimer limit; on expiry the
-//    CTA records TQR_ERR_TIMEOUT in the status word and returns.
-//  * FP64 arithmetic runs on the DFMA pipe (sm_103 has no FP64 tensor path
-//    faster than DFMA), so the kernels apply Householder reflectors one at a
-//    time: no T-factor products are spent on the critical path, and every
-//    flop is one the LAPACK count includes.  ib only sets how many reflectors
-//    are staged in shared memory at once (and the block size of T).
-//  * An update kernel works on a strip of W = 256/G columns held in shared
-//    memory.  Thread (c, g) owns column c and the rows r = g (mod G) of the
-//    strip, so a reflector's dot product is a G-lane shuffle reduction and no
-//    thread ever reads a row another thread writes.
-#include "tqr_internal.h"
-#include "../../include/tqr.h"
-
-#include <cuda_runtime.h>
-#include <cstdint>
+// Host side of libtqr's executor: layout choice, launch of the persistent
+// executor (its instantiations live in exec_inst.cu), the initialization
+// kernel of the dependency counters and the on-demand T-factor kernel.
+#include "executor.cuh"
 
 namespace tqr {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-enum Mode { GE = 0, TT = 1, TS = 2 };
-
-// ------------------------------------------------------------ memory order
-__device__ __forceinline__ int ld_acquire(const int32_t* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int32_t* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int atom_add_acq_rel(int32_t* p, int v) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void set_status(int32_t* status, int code) {
-    atomicCAS(status, 0, code);
-}
-
-// ------------------------------------------------------------ smem layout
-struct Smem {
-    double* Cs;    // strip: nb x W, leading dimension ldc
-    double* Vs;    // reflector block: nb x ib, leading dimension nb
-    double* Ct;    // top rows: ib x max(W, ib), leading dimension ldt
-    double* taus;  // ib
-    int ldc, ldt;
-};
-
-__host__ __device__ inline int round16(int x) { return (x + 15) / 16 * 16; }
-__host__ __device__ inline int ldc_of(int nb, int G) { return round16(nb) + (G % 16); }
-
-__host__ __device__ inline int smem_doubles(int nb, int ib, int G) {
-    const int W = kThreads / G;
-    const int wt = W > ib ? W : ib;
-    return ldc_of(nb, G) * W + nb * ib + (ib + 1) * wt + ib;
-}
-
-template <int G>
-__device__ __forceinline__ Smem layout(const ExecParams& P, double* base) {
-    constexpr int W = kThreads / G;
-    Smem s;
-    s.ldc = ldc_of(P.nb, G);
-    s.ldt = P.ib + 1;
-    s.Cs = base;
-    s.Vs = s.Cs + s.ldc * W;
-    s.Ct = s.Vs + P.nb * P.ib;
-    const int wt = W > P.ib ? W : P.ib;
-    s.taus = s.Ct + s.ldt * wt;
-    return s;
-}
-
-// A view of (a window of) a column-major matrix with validity bounds: rows
-// >= rv and columns >= cv do not exist (they read as zero, never written).
-struct View {
-    double* p;
-    int64_t ld;
-    int rv, cv;
-};
-
-__device__ __forceinline__ View tile_view(const ExecParams& P, int i, int k) {
-    View v;
-    v.p = P.A + static_cast<int64_t>(k) * P.nb * P.lda + static_cast<int64_t>(i) * P.nb;
-    v.ld = P.lda;
-    const int64_t rr = P.m - static_cast<int64_t>(i) * P.nb;
-    const int64_t cc = P.n - static_cast<int64_t>(k) * P.nb;
-    v.rv = static_cast<int>(rr < P.nb ? rr : P.nb);
-    v.cv = static_cast<int>(cc < P.nb ? cc : P.nb);
-    return v;
-}
-
-// Row block i of the right-hand side B, columns from c0.
-__device__ __forceinline__ View rhs_view(const ExecParams& P, int i, int c0) {
-    View v;
-    v.p = P.B + static_cast<int64_t>(c0) * P.ldb + static_cast<int64_t>(i) * P.nb;
-    v.ld = P.ldb;
-    const int64_t rr = P.m - static_cast<int64_t>(i) * P.nb;
-    const int64_t cc = P.nrhs - c0;
-    v.rv = static_cast<int>(rr < P.nb ? rr : P.nb);
-    v.cv = static_cast<int>(cc < 0x40000000 ? cc : 0x40000000);
-    return v;
-}
-
-// dst[(r - rbase) + c*ldd] = src(r, c0 + c) for r in [r0, r1), c in [0, nc).
-// Each thread keeps eight loads in flight before storing them.
-__device__ __forceinline__ void load_rect(double* dst, int ldd, int rbase, const View& v, int r0,
-                                          int r1, int c0, int nc) {
-    const int nr = r1 - r0;
-    if (nr <= 0) return;
-    const int total = nr * nc;
-    for (int base = threadIdx.x; base < total; base += 8 * kThreads) {
-        double x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * kThreads;
-            const int r = r0 + idx % nr;
-            const int c = idx / nr;
-            x[u] = (idx < total && r < v.rv && c0 + c < v.cv)
-                       ? __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * kThreads;
-            if (idx < total) dst[(r0 + idx % nr - rbase) + (idx / nr) * ldd] = x[u];
-        }
-    }
-}
-
-// src(r, c0 + c) = dst[...] for the same rectangle; upper = only r <= c0 + c.
-__device__ __forceinline__ void store_rect(const double* src, int lds, int rbase, const View& v,
-                                           int r0, int r1, int c0, int nc, bool upper) {
-    const int nr = r1 - r0;
-    if (nr <= 0) return;
-    for (int idx = threadIdx.x; idx < nr * nc; idx += kThreads) {
-        const int r = r0 + idx % nr;
-        const int c = idx / nr;
-        if (r < v.rv && c0 + c < v.cv && (!upper || r <= c0 + c))
-            v.p[r + static_cast<int64_t>(c0 + c) * v.ld] = src[(r - rbase) + c * lds];
-    }
-}
-
-template <int G>
-__device__ __forceinline__ double group_sum(double x) {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-
-// ----------------------------------------------------------------------------
-// Apply reflectors j0..j0+ib-1 (staged in Vs/taus) to the strip in Cs (and
-// the top rows in Ct for TT/TS), forward (Q^T) or backward (Q).
-//   GE: reflector j is (1 at row j, Vs[r>j]) on the strip's own rows;
-//   TT: (1 at top row j, Vs[0..j] on the bottom rows);
-//   TS: (1 at top row j, Vs[0..nb-1] on the bottom rows).
-// Thread (c, g) owns column c and rows r = g (mod G): no shared-memory
-// hazards between threads, only the G-lane reductions.
-// ----------------------------------------------------------------------------
-template <int G, int MODE>
-__device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int ib, int trans, int ncols) {
-    const int c = threadIdx.x / G;
-    const int g = threadIdx.x % G;
-    if ((threadIdx.x / 32) * (32 / G) >= ncols) return;   // this warp's columns do not exist
-    double* Cc = S.Cs + c * S.ldc;
-    for (int s = 0; s < ib; ++s) {
-        const int jj = trans ? s : ib - 1 - s;
-        const int j = j0 + jj;
-        const double tau = S.taus[jj];
-        const double* v = S.Vs + jj * nb;
-        int rlo, rhi;   // own rows r in [rlo, rhi), r = g (mod G)
-        double acc;
-        if (MODE == GE) {
-            rlo = j + 1 + ((g - j - 1) & (G - 1));
-            rhi = nb;
-            acc = (g == (j & (G - 1))) ? Cc[j] : 0.0;
-        } else {
-            rlo = g;
-            rhi = (MODE == TT) ? j + 1 : nb;
-            acc = (g == 0) ? S.Ct[jj + c * S.ldt] : 0.0;
-        }
-        double acc2 = 0.0;
-        int r = rlo;
-        for (; r + G < rhi; r += 2 * G) {
-            acc = fma(v[r], Cc[r], acc);
-            acc2 = fma(v[r + G], Cc[r + G], acc2);
-        }
-        if (r < rhi) acc = fma(v[r], Cc[r], acc);
-        acc = group_sum<G>(acc + acc2);
-        const double w = tau * acc;
-        if (MODE == GE) {
-            if (g == (j & (G - 1))) Cc[j] -= w;
-        } else {
-            if (g == 0) S.Ct[jj + c * S.ldt] -= w;
-        }
-        for (r = rlo; r < rhi; r += G) Cc[r] = fma(-v[r], w, Cc[r]);
-    }
-}
-
-// ----------------------------------------------------------------------------
-// Householder panel factorization of the ib columns staged in Vs (and Ct for
-// TT/TS).  Reflector j maps (alpha, x) to (beta, 0), LAPACK convention:
-// beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha)/beta,
-// v = x / (alpha - beta); x = 0 gives tau = 0.
-//   GE: alpha = Vs[j, jj], x = Vs[j+1.., jj]   (GEQRT)
-//   TT: alpha = Ct[jj, jj], x = Vs[0..j, jj]   (TTQRT)
-//   TS: alpha = Ct[jj, jj], x = Vs[0..nb-1, jj] (TSQRT)
-// Warp 0 forms reflector 0.  Then, for each reflector jj, warp 0 applies it to
-// column jj+1 and at once forms reflector jj+1 from that column, while warps
-// 1..7 apply reflector jj to columns jj+2.. of the block: one block barrier
-// per reflector, and reflector generation overlaps the other columns' updates.
-// ----------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ void fb_range(int j, int nb, int* rlo, int* rhi) {
-    *rlo = (MODE == GE) ? j + 1 : 0;
-    *rhi = (MODE == TT) ? j + 1 : nb;
-}
-
-// Warp-level: forms reflector jj of the block from column jj of Vs (and its
-// alpha), writes beta over alpha, tau into S.taus[jj], and v in place.
-template <int MODE>
-__device__ void fb_form(const Smem& S, int nb, int j0, int jj, int lane, int32_t* status) {
-    const int j = j0 + jj;
-    double* v = S.Vs + jj * nb;
-    int rlo, rhi;
-    fb_range<MODE>(j, nb, &rlo, &rhi);
-    double sig = 0.0;
-    for (int r = rlo + lane; r < rhi; r += 32) sig = fma(v[r], v[r], sig);
-    sig = warp_sum(sig);
-    double scale = 0.0;
-    if (lane == 0) {
-        double* ap = (MODE == GE) ? &v[j] : &S.Ct[jj + jj * S.ldt];
-        const double alpha = *ap;
-        double tau = 0.0;
-        if (sig != 0.0 || !isfinite(sig)) {
-            const double nrm = sqrt(fma(alpha, alpha, sig));
-            if (!isfinite(nrm)) set_status(status, TQR_ERR_NONFINITE);
-            const double beta = alpha >= 0.0 ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
-            *ap = beta;
-        }                                   // else x is zero: identity reflector, zero tail
-        S.taus[jj] = tau;
-    }
-    scale = __shfl_sync(kFull, scale, 0);
-    for (int r = rlo + lane; r < rhi; r += 32) v[r] *= scale;
-}
-
-// Warp-level: applies reflector jj (v in column jj, tau) to column cc of the block.
-template <int MODE>
-__device__ __forceinline__ void fb_apply(const Smem& S, int nb, int j0, int jj, int cc, double tau, int lane) {
-    const int j = j0 + jj;
-    const double* v = S.Vs + jj * nb;
-    double* u = S.Vs + cc * nb;
-    int rlo, rhi;
-    fb_range<MODE>(j, nb, &rlo, &rhi);
-    double acc = 0.0;
-    for (int r = rlo + lane; r < rhi; r += 32) acc = fma(v[r], u[r], acc);
-    if (lane == 0) acc += (MODE == GE) ? u[j] : S.Ct[jj + cc * S.ldt];
-    acc = warp_sum(acc);
-    const double w = tau * acc;
-    if (lane == 0) {
-        if (MODE == GE) u[j] -= w;
-        else S.Ct[jj + cc * S.ldt] -= w;
-    }
-    for (int r = rlo + lane; r < rhi; r += 32) u[r] = fma(-v[r], w, u[r]);
-}
-
-template <int MODE>
-__device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* status) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    constexpr int kWarps = kThreads / 32;
-    if (warp == 0) fb_form<MODE>(S, nb, j0, 0, lane, status);
-    __syncthreads();
-    for (int jj = 0; jj < ib; ++jj) {
-        const double tau = S.taus[jj];
-        if (warp == 0) {
-            if (jj + 1 < ib) {
-                fb_apply<MODE>(S, nb, j0, jj, jj + 1, tau, lane);
-                __syncwarp();
-                fb_form<MODE>(S, nb, j0, jj + 1, lane, status);
-            }
-        } else {
-            for (int cc = jj + 1 + warp; cc < ib; cc += kWarps - 1) fb_apply<MODE>(S, nb, j0, jj, cc, tau, lane);
-        }
-        __syncthreads();
-    }
-}
-
-template <int MODE>
-__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch);
-template <int G, int MODE, int PREC>
-__device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
-                                  int ncol, double* smem);
-
-// ----------------------------------------------------------------------------
-// Panel kernels: GEQRT(i,k) (MODE GE), TTQRT(i,piv,k) (TT), TSQRT(i,piv,k)
-// (TS).  Blocks of ib columns are factored in turn; after each block its
-// reflectors are applied to the rest of the tile (pair), W columns at a time.
-// ----------------------------------------------------------------------------
-template <int G, int MODE, int PREC>
-__device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* smem) {
-    constexpr int W = kThreads / G;
-    const Smem S = layout<G>(P, smem);
-    const int nb = P.nb, ib = P.ib;
-    const View bot = tile_view(P, i, k);                    // GE: the tile itself
-    const View top = (MODE == GE) ? bot : tile_view(P, piv, k);
-    double* tau_out = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
-    const int ncol = bot.cv;                                // valid columns of the tile pair
-    for (int j0 = 0; j0 < nb; j0 += ib) {
-        // Stage the panel block.
-        __syncthreads();
-        if (MODE == GE) {
-            load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
-        } else {
-            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib);
-            load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
-        }
-        __syncthreads();
-        factor_block<MODE>(S, nb, j0, ib, P.status);
-        // Write the block back: R (and V) in place, tau to the handle.
-        if (MODE == GE) {
-            store_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib, false);
-        } else {
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib, true);
-            store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
-        }
-        for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
-        if (PREC != 0) {
-            // T_b in FP64 (Cs is free here), then the trailing columns of the
-            // tile pair on the tensor cores.
-            const int64_t tile = static_cast<int64_t>(k) * P.p + i;
-            float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
-            float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
-            for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
-                const int r = idx % nb, jj = idx / nb, j = j0 + jj;
-                float v;
-                if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * nb]));
-                else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * nb]) : 0.0f;
-                else v = static_cast<float>(S.Vs[r + jj * nb]);
-                Vdst[r + static_cast<int64_t>(j) * nb] = v;
-            }
-            form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
-            panel_lp_trailing<G, MODE, PREC>(P, i, k, top, bot, j0, ncol, smem);
-        } else {
-            // Trailing update of the columns right of the block.
-            for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
-                __syncthreads();
-                if (MODE == GE) {
-                    load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
-                } else {
-                    load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-                    load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
-                }
-                __syncthreads();
-                apply_block<G, MODE>(S, nb, j0, ib, 1, ncol - c0);
-                __syncthreads();
-                if (MODE == GE) {
-                    store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
-                } else {
-                    store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
-                    store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
-                }
-            }
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------
-// Update kernels on one strip: UNMQR (GE), TTMQR (TT), TSMQR (TS).  The
-// reflectors come from tile (i,k); the strip is columns [strip*W, +W) of
-// tile column j (rows i and piv), or of the right-hand side B.
-// ----------------------------------------------------------------------------
-template <int G, int MODE>
-__device__ void update_task(const ExecParams& P, const DevTask& T, double* smem) {
-    constexpr int W = kThreads / G;
-    const Smem S = layout<G>(P, smem);
-    const int nb = P.nb, ib = P.ib;
-    const View vt = tile_view(P, T.i, T.k);
-    const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(T.k) * P.p + T.i) * nb;
-    const int c0 = T.strip * W;
-    View bot, top;
-    if (P.B) {
-        bot = rhs_view(P, T.i, 0);
-        top = (MODE == GE) ? bot : rhs_view(P, T.piv, 0);
-    } else {
-        bot = tile_view(P, T.i, T.j);
-        top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
-    }
-    const int vrows_hi = nb;
-    load_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W);
-    const int nblk = nb / ib;
-    for (int bb = 0; bb < nblk; ++bb) {
-        const int b = P.trans ? bb : nblk - 1 - bb;
-        const int j0 = b * ib;
-        __syncthreads();
-        if (MODE == GE) load_rect(S.Vs, nb, 0, vt, j0, vrows_hi, j0, ib);
-        else load_rect(S.Vs, nb, 0, vt, 0, (MODE == TT) ? j0 + ib : vrows_hi, j0, ib);
-        for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
-        if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-        __syncthreads();
-        apply_block<G, MODE>(S, nb, j0, ib, P.trans, bot.cv - c0);
-        if (MODE != GE) {
-            __syncthreads();
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
-        }
-    }
-    __syncthreads();
-    store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
-}
-
-
-// ----------------------------------------------------------------------------
-// Mixed precision (split-TF32 or TF32 updates, FP64 panels).
-//
-// A panel task also forms, in FP64, the compact-WY factor T_b of each block
-// of ib reflectors (Schreiber-Van Loan forward accumulation) and stores it in
-// the handle's T array.  An update task then applies block b as
-//     C <- C - V_b (T_b^T (V_b^T C))            (GE: UNMQR)
-//     [C_top; C] <- ... with V = [I; V_b]       (TT/TS: TTMQR/TSMQR)
-// with both products on the tensor cores (mma.sync m16n8k8 TF32, FP32
-// accumulation).  Split-TF32 writes each operand x = hi + lo (hi = tf32(x),
-// lo = tf32(x - hi)) and sums hi*hi + hi*lo + lo*hi.  C stays in FP64.
-// ----------------------------------------------------------------------------
-template <int MODE>
-__device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch) {
-    double* Gm = scratch;             // ib x ib Gram of the block's full reflector vectors
-    double* Tb = scratch + ib * ib;   // ib x ib T
-    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) {
-        const int r = idx % ib, c = idx / ib;
-        double s = 0.0;
-        if (r < c) {
-            const double* vr = S.Vs + r * nb;
-            const double* vc = S.Vs + c * nb;
-            const int jr = j0 + r, jc = j0 + c;
-            if (MODE == GE) {
-                s = vr[jc];                                  // tail of r . unit entry of c
-                for (int x = jc + 1; x < nb; ++x) s = fma(vr[x], vc[x], s);
-            } else {
-                const int hi = (MODE == TT) ? jr + 1 : nb;   // support of the tail of r
-                for (int x = 0; x < hi; ++x) s = fma(vr[x], vc[x], s);
-            }
-        }
-        Gm[idx] = s;
-        Tb[idx] = 0.0;
-    }
-    __syncthreads();
-    for (int c = 0; c < ib; ++c) {
-        const double tc = S.taus[c];
-        for (int r = threadIdx.x; r < c; r += kThreads) {
-            double s = 0.0;
-            for (int x = r; x < c; ++x) s = fma(Tb[r + x * ib], Gm[x + c * ib], s);
-            Tb[r + c * ib] = -tc * s;
-        }
-        if (threadIdx.x == 0) Tb[c + c * ib] = tc;
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) Tout[idx] = static_cast<float>(Tb[idx]);
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// D += A * B with A = ahi + alo, B = bhi + blo (PREC 1: three products; 2: one).
-template <int PREC>
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ahi)[4], const uint32_t (&alo)[4],
-                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-    if (PREC == 1) {
-        mma_tf32(d, alo, bh0, bh1);
-        mma_tf32(d, ahi, bl0, bl1);
-    }
-    mma_tf32(d, ahi, bh0, bh1);
-}
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// TF32 split by truncation on the integer pipe: hi keeps the top 19 bits of x,
-// lo the top 19 bits of x - hi (exact in FP32).  PREC 2: hi only.
-template <int PREC>
-__device__ __forceinline__ void split_t(float x, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(x) & 0xffffe000u;
-    lo = (PREC == 1) ? (__float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u) : 0u;
-}
-
-// Layout of an update task in low precision: the strip of C and the strip of
-// the top tile (TT/TS) in FP32, two buffers of the FP32 reflector block and of
-// its T, and W / T^T W.
-struct Lp2 {
-    float* Cf;
-    float* Ctf;
-    float* Vb[2];
-    float* Tb[2];
-    float* Wm;
-    float* W2;
-    int ldc, ldv, ldw;
-};
-
-__host__ __device__ inline int lp2_ldc(int nb) { return (nb + 31) / 32 * 32 + 4; }
-__host__ __device__ inline int lp2_ldv(int nb) { return (nb + 15) / 16 * 16 + 4; }
-__host__ __device__ inline int lp2_bytes(int nb, int ib, int G) {
-    const int W = kThreads / G;
-    return 4 * (2 * lp2_ldc(nb) * W + 2 * lp2_ldv(nb) * ib + 2 * ib * ib + 2 * ib * (W + 8));
-}
-
-template <int G>
-__device__ __forceinline__ Lp2 lp2_layout(int nb, int ib, double* base) {
-    constexpr int W = kThreads / G;
-    Lp2 L;
-    L.ldc = lp2_ldc(nb);
-    L.ldv = lp2_ldv(nb);
-    L.ldw = W + 8;
-    float* f = reinterpret_cast<float*>(base);
-    L.Cf = f;
-    L.Ctf = L.Cf + L.ldc * W;
-    L.Vb[0] = L.Ctf + L.ldc * W;
-    L.Vb[1] = L.Vb[0] + L.ldv * ib;
-    L.Tb[0] = L.Vb[1] + L.ldv * ib;
-    L.Tb[1] = L.Tb[0] + ib * ib;
-    L.Wm = L.Tb[1] + ib * ib;
-    L.W2 = L.Wm + ib * L.ldw;
-    return L;
-}
-
-// Rows [r0, r1) of a strip of a column-major FP64 view <-> FP32 shared memory.
-__device__ __forceinline__ void strip_to_f32(float* dst, int ldd, const View& v, int r0, int r1, int c0, int W) {
-    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        const bool rok = r < v.rv;
-#pragma unroll 8
-        for (int c = 0; c < W; ++c) {
-            double x = 0.0;
-            if (rok && c0 + c < v.cv) x = __ldcg(v.p + r + static_cast<int64_t>(c0 + c) * v.ld);
-            dst[r + c * ldd] = static_cast<float>(x);
-        }
-    }
-}
-__device__ __forceinline__ void strip_from_f32(const float* src, int lds, const View& v, int r0, int r1, int c0,
-                                               int W) {
-    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        if (r >= v.rv) continue;
-#pragma unroll 8
-        for (int c = 0; c < W; ++c)
-            if (c0 + c < v.cv) v.p[r + static_cast<int64_t>(c0 + c) * v.ld] = static_cast<double>(src[r + c * lds]);
-    }
-}
-
-// One block of ib reflectors (FP32 V_b in Vb, T_b in Tb) applied to the FP32
-// strip L.Cf (rows [rlo, rhi)) and, for TT/TS, to rows j0.. of L.Ctf:
-//   W = V_b^T C (+ C_top rows),  W2 = T_b^T W,  C_top rows -= W2,  C -= V_b W2.
-// Both products run on the tensor cores (m16n8k8 TF32, FP32 accumulation).
-template <int G, int MODE, int PREC>
-__device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib, int j0, int rlo, int rhi) {
-    constexpr int W = kThreads / G;
-    constexpr int NNT = W / 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int nmt1 = ib / 16;
-        // W = V_b^T C: warp w owns m-tile w % nmt1 and n-tiles (w / nmt1) + (8 / nmt1) t.
-        {
-            const int m0 = (warp % nmt1) * 16;
-            constexpr int kMaxAcc = 8;
-            float acc[kMaxAcc][4];
-            const int nstep = 8 / nmt1;
-#pragma unroll
-            for (int a = 0; a < kMaxAcc; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
-            for (int k0 = rlo; k0 < rhi; k0 += 8) {
-                uint32_t ahi[4], alo[4];
-                split_t<PREC>(Vb[(k0 + tig) + (m0 + gid) * L.ldv], ahi[0], alo[0]);
-                split_t<PREC>(Vb[(k0 + tig) + (m0 + gid + 8) * L.ldv], ahi[1], alo[1]);
-                split_t<PREC>(Vb[(k0 + tig + 4) + (m0 + gid) * L.ldv], ahi[2], alo[2]);
-                split_t<PREC>(Vb[(k0 + tig + 4) + (m0 + gid + 8) * L.ldv], ahi[3], alo[3]);
-#pragma unroll
-                for (int a = 0; a < kMaxAcc; ++a) {
-                    const int nt = warp / nmt1 + a * nstep;
-                    if (a * nstep < NNT && nt < NNT) {
-                        const int n0 = nt * 8;
-                        uint32_t bh0, bl0, bh1, bl1;
-                        split_t<PREC>(L.Cf[(k0 + tig) + (n0 + gid) * L.ldc], bh0, bl0);
-                        split_t<PREC>(L.Cf[(k0 + tig + 4) + (n0 + gid) * L.ldc], bh1, bl1);
-                        mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
-                    }
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < kMaxAcc; ++a) {
-                const int nt = warp / nmt1 + a * nstep;
-                if (a * nstep < NNT && nt < NNT) {
-                    const int n0 = nt * 8;
-                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig] = acc[a][0];
-                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig + 1] = acc[a][1];
-                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig] = acc[a][2];
-                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig + 1] = acc[a][3];
-                }
-            }
-        }
-        __syncthreads();
-        // W2 = T^T (W + C_top rows)
-        for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
-            const int a = idx / W, n = idx % W;
-            float sum = 0.0f;
-            for (int x = 0; x <= a; ++x) {
-                float w = L.Wm[x * L.ldw + n];
-                if (MODE != GE) w += L.Ctf[(j0 + x) + n * L.ldc];
-                sum = fmaf(Tb[x + a * ib], w, sum);
-            }
-            L.W2[a * L.ldw + n] = sum;
-        }
-        __syncthreads();
-        if (MODE != GE)
-            for (int idx = threadIdx.x; idx < ib * W; idx += kThreads) {
-                const int a = idx / W, n = idx % W;
-                L.Ctf[(j0 + a) + n * L.ldc] -= L.W2[a * L.ldw + n];
-            }
-        // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...
-        for (int mt = (rlo / 16) + warp; mt < rhi / 16; mt += 8) {
-            const int r0 = mt * 16;
-            for (int nt = 0; nt < NNT; ++nt) {
-                const int n0 = nt * 8;
-                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                for (int k0 = 0; k0 < ib; k0 += 8) {
-                    uint32_t ahi[4], alo[4];
-                    split_t<PREC>(Vb[(r0 + gid) + (k0 + tig) * L.ldv], ahi[0], alo[0]);
-                    split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig) * L.ldv], ahi[1], alo[1]);
-                    split_t<PREC>(Vb[(r0 + gid) + (k0 + tig + 4) * L.ldv], ahi[2], alo[2]);
-                    split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig + 4) * L.ldv], ahi[3], alo[3]);
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split_t<PREC>(L.W2[(k0 + tig) * L.ldw + n0 + gid], bh0, bl0);
-                    split_t<PREC>(L.W2[(k0 + tig + 4) * L.ldw + n0 + gid], bh1, bl1);
-                    mma3<PREC>(acc, ahi, alo, bh0, bh1, bl0, bl1);
-                }
-                L.Cf[(r0 + gid) + (n0 + 2 * tig) * L.ldc] -= acc[0];
-                L.Cf[(r0 + gid) + (n0 + 2 * tig + 1) * L.ldc] -= acc[1];
-                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig) * L.ldc] -= acc[2];
-                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig + 1) * L.ldc] -= acc[3];
-            }
-        }
-}
-
-// Update task in low precision: C (and C_top) converted to FP32 once, every
-// block of ib reflectors applied with two tensor-core products,
-//   W = V_b^T C (+ C_top rows),  W2 = T_b^T W,  C_top rows -= W2,  C -= V_b W2,
-// then converted back.  Reflector blocks and T arrive in FP32 from the panel
-// task (unit/zero structure written out) by double-buffered cp.async.
-template <int G, int MODE, int PREC>
-__device__ void update_task_lp(const ExecParams& P, const DevTask& T, double* smem) {
-    constexpr int W = kThreads / G;
-    const int nb = P.nb, ib = P.ib;
-    const Lp2 L = lp2_layout<G>(nb, ib, smem);
-    const int64_t tile = static_cast<int64_t>(T.k) * P.p + T.i;
-    const float* Vt = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
-    const float* Tt = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
-    const int c0 = T.strip * W;
-    const View bot = tile_view(P, T.i, T.j);
-    const View top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
-    const int nblk = nb / ib;
-
-    auto stage = [&](int b, int buf) {
-        const int j0 = b * ib;
-        const int rlo = (MODE == GE) ? j0 : 0;
-        const int rhi = (MODE == TT) ? j0 + ib : nb;
-        const int chunks = (rhi - rlo) / 4;
-        for (int idx = threadIdx.x; idx < chunks * ib; idx += kThreads) {
-            const int jj = idx / chunks, c = idx % chunks;
-            cp_async16(L.Vb[buf] + rlo + 4 * c + jj * L.ldv, Vt + rlo + 4 * c + static_cast<int64_t>(j0 + jj) * nb);
-        }
-        for (int idx = threadIdx.x; idx < ib * ib / 4; idx += kThreads)
-            cp_async16(L.Tb[buf] + 4 * idx, Tt + static_cast<int64_t>(j0) * ib + 4 * idx);
-        cp_commit();
-    };
-
-    stage(0, 0);
-    strip_to_f32(L.Cf, L.ldc, bot, 0, nb, c0, W);
-    if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, 0, nb, c0, W);
-    for (int b = 0; b < nblk; ++b) {
-        const int buf = b & 1;
-        const int j0 = b * ib;
-        const int rlo = (MODE == GE) ? j0 : 0;
-        const int rhi = (MODE == TT) ? j0 + ib : nb;
-        if (b + 1 < nblk) {
-            stage(b + 1, buf ^ 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
-        lp2_block<G, MODE, PREC>(L, L.Vb[buf], L.Tb[buf], ib, j0, rlo, rhi);
-        __syncthreads();
-    }
-    strip_from_f32(L.Cf, L.ldc, bot, 0, nb, c0, W);
-    if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, 0, nb, c0, W);
-}
-
-// Trailing update of a panel task in low precision: block j0's FP32 V and T
-// (just written to the handle) come back by cp.async; the trailing columns
-// [j0+ib, ncol) of the tile pair are converted to FP32 strip by strip and
-// updated on the tensor cores.  The whole shared memory is free here.
-template <int G, int MODE, int PREC>
-__device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
-                                  int ncol, double* smem) {
-    constexpr int W = kThreads / G;
-    const int nb = P.nb, ib = P.ib;
-    const Lp2 L = lp2_layout<G>(nb, ib, smem);
-    const int64_t tile = static_cast<int64_t>(k) * P.p + i;
-    const float* Vt = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
-    const float* Tt = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
-    const int rlo = (MODE == GE) ? j0 : 0;
-    const int rhi = (MODE == TT) ? j0 + ib : nb;
-    __syncthreads();                       // the block's V / T writes are done
-    const int chunks = (rhi - rlo) / 4;
-    for (int idx = threadIdx.x; idx < chunks * ib; idx += kThreads) {
-        const int jj = idx / chunks, c = idx % chunks;
-        cp_async16(L.Vb[0] + rlo + 4 * c + jj * L.ldv, Vt + rlo + 4 * c + static_cast<int64_t>(j0 + jj) * nb);
-    }
-    for (int idx = threadIdx.x; idx < ib * ib / 4; idx += kThreads)
-        cp_async16(L.Tb[0] + 4 * idx, Tt + static_cast<int64_t>(j0) * ib + 4 * idx);
-    cp_commit();
-    cp_wait<0>();
-    for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
-        __syncthreads();
-        strip_to_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
-        if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
-        __syncthreads();
-        lp2_block<G, MODE, PREC>(L, L.Vb[0], L.Tb[0], ib, j0, rlo, rhi);
-        __syncthreads();
-        strip_from_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
-        if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
-    }
-}
-
-template <int G, int MODE, int PREC>
-__device__ __forceinline__ void update_any(const ExecParams& P, const DevTask& T, double* smem) {
-    if (PREC != 0 && !P.B) update_task_lp<G, MODE, (PREC != 0 ? PREC : 1)>(P, T, smem);
-    else update_task<G, MODE>(P, T, smem);
-}
-
-template <int G, int PREC>
-__device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
-    switch (T.kind & 0xff) {
-        case GEQRT: panel_task<G, GE, PREC>(P, T.i, -1, T.k, smem); break;
-        case TTQRT: panel_task<G, TT, PREC>(P, T.i, T.piv, T.k, smem); break;
-        case TSQRT: panel_task<G, TS, PREC>(P, T.i, T.piv, T.k, smem); break;
-        case UNMQR: update_any<G, GE, PREC>(P, T, smem); break;
-        case TTMQR: update_any<G, TT, PREC>(P, T, smem); break;
-        case TSMQR: update_any<G, TS, PREC>(P, T, smem); break;
-        default: set_status(P.status, TQR_ERR_INTERNAL); break;
-    }
-}
-
-// Warp 0: decrement the successors of task t; push those that become ready.
-__device__ void release_successors(const ExecParams& P, int t) {
-    const int lane = threadIdx.x & 31;
-    __threadfence();                      // the CTA's writes before the counters
-    const int b = P.succ_ptr[t], e = P.succ_ptr[t + 1];
-    for (int base = b; base < e; base += 32) {
-        const int idx = base + lane;
-        int s = -1;
-        bool ready = false;
-        if (idx < e) {
-            s = P.succ[idx];
-            ready = atom_add_acq_rel(&P.deps[s], -1) == 1;
-        }
-        const unsigned mask = __ballot_sync(kFull, ready);
-        if (mask) {
-            const int leader = __ffs(mask) - 1;
-            unsigned pos = 0;
-            if (lane == leader) pos = atomicAdd(&P.ctr[1], static_cast<unsigned>(__popc(mask)));
-            pos = __shfl_sync(kFull, pos, leader);
-            if (ready) {
-                const unsigned rank = __popc(mask & ((1u << lane) - 1u));
-                if (pos + rank < static_cast<unsigned>(P.ntasks)) st_release(&P.queue[pos + rank], s);
-                else set_status(P.status, TQR_ERR_INTERNAL);
-            }
-        }
-    }
-}
-
-template <int G, int PREC>
-__global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
-    extern __shared__ __align__(16) double smem[];
-    __shared__ int s_task;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int t = -1;
-            const unsigned slot = atomicAdd(&P.ctr[0], 1u);
-            if (slot < static_cast<unsigned>(P.ntasks)) {
-                const uint64_t t0 = globaltimer();
-                unsigned it = 0;
-                for (;;) {
-                    t = ld_acquire(&P.queue[slot]);
-                    if (t >= 0) break;
-                    if (ld_relaxed(P.status) != 0) break;
-                    if ((++it & 31u) == 0 && globaltimer() - t0 > P.timeout_ns) {
-                        set_status(P.status, TQR_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                if (t >= P.ntasks) {
-                    set_status(P.status, TQR_ERR_INTERNAL);
-                    t = -1;
-                }
-                if (t >= 0) __threadfence();
-            }
-            s_task = t;
-        }
-        __syncthreads();
-        const int t = s_task;
-        if (t < 0) return;
-        const DevTask T = P.tasks[t];
-        uint64_t t_begin = 0;
-        if (P.trace && threadIdx.x == 0) t_begin = globaltimer();
-        if (P.mats) {
-            ExecParams Q = P;
-            const MatDesc d = P.mats[T.kind >> 8];
-            Q.A = d.A;
-            Q.lda = d.lda;
-            Q.m = d.m;
-            Q.n = d.n;
-            Q.nb = d.nb;
-            Q.ib = d.ib;
-            Q.p = d.p;
-            Q.q = d.q;
-            Q.tau_ge = P.tau_ge + d.tau_off;
-            Q.tau_el = P.tau_el + d.tau_off;
-            run_task<G, PREC>(Q, T, smem);
-        } else {
-            run_task<G, PREC>(P, T, smem);
-        }
-        __syncthreads();
-        if (P.trace && threadIdx.x == 0) {
-            uint32_t sm;
-            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-            P.trace[2 * t] = t_begin;
-            P.trace[2 * t + 1] = ((globaltimer() - t_begin) & 0x00ffffffffffffffull) | (static_cast<uint64_t>(sm) << 56);
-        }
-        if (threadIdx.x < 32) release_successors(P, t);
-    }
-}
 
 __global__ void init_kernel(int32_t* deps, const int32_t* indeg, int32_t* queue, const int32_t* ready,
                             int nready, int ntasks, uint32_t* ctr, int32_t* status, int reset) {
@@ -993,20 +125,12 @@ int device_sm_count() {
     return n;
 }
 
-template <int G, int PREC>
-static cudaError_t launch_gp(const ExecParams& P, int smem, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(exec_kernel<G, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    exec_kernel<G, PREC><<<grid, kThreads, smem, s>>>(P);
-    return cudaGetLastError();
-}
-
 template <int G>
 static cudaError_t launch_g(const ExecParams& P, int smem, int grid, cudaStream_t s) {
     switch (P.B ? 0 : P.prec) {      // apply graphs always run the FP64 kernels
-        case 0: return launch_gp<G, 0>(P, smem, grid, s);
-        case 1: return launch_gp<G, 1>(P, smem, grid, s);
-        case 2: return launch_gp<G, 2>(P, smem, grid, s);
+        case 0: return launch_exec<G, 0>(P, smem, grid, s);
+        case 1: return launch_exec<G, 1>(P, smem, grid, s);
+        case 2: return launch_exec<G, 2>(P, smem, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -128,11 +128,15 @@ bool lp_supported(int nb, int ib, int G);
 int strip_width(int G);
 int fp64_smem_bytes(int nb, int ib, int G);
 int device_sm_count();
+// exec_kernel<G, PREC> launcher; one definition per (G, PREC) in its own object.
+template <int G, int PREC>
+cudaError_t launch_exec(const ExecParams& P, int smem, int grid, cudaStream_t s);
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,
                                int smem, bool reset_status, cudaStream_t s);
-// Batched FlatTree-TS for one tile column (q = 1): one CTA per matrix, R in
-// shared memory.  A matrix of n <= 128 columns with n <= nb runs there when its
-// shared memory (tile of nb rows, packed R) fits; ncol_class is 32, 64 or 128.
+// Batched FlatTree-TS for one tile column (q = 1): one CTA per matrix, the tile
+// in registers, R in shared memory.  A matrix of n <= 128 columns with n <= nb
+// and nb in {64, 128, 256} (nb >= its column class 32 / 64 / 128; FP64 with
+// class 128 needs nb = 128) runs there when its shared memory fits.
 struct Ts1Desc {
     void* A;            // column-major, leading dimension m (double or float)
     int64_t m;
@@ -140,9 +144,9 @@ struct Ts1Desc {
     int64_t tau_off;    // offset of the matrix's tau block (p * nb entries)
 };
 int ts1_ncol_class(int64_t n);
-int ts1_smem_bytes(int ncol_class, int hmax, int elem_size);
+int ts1_smem_bytes(int ncol_class, int h, int elem_size);
 bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size);
-cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int hmax, bool f32, void* tau_ge,
+cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int h, bool f32, void* tau_ge,
                        void* tau_el, int32_t* status, cudaStream_t s);
 // T factors of the listed panel tasks (kind, i, k triplets on the device).
 cudaError_t launch_form_t(const ExecParams& P, const int32_t* panels, int npanels,

@@ -15,13 +15,19 @@
 // get tau = 0).
 //
 // Reflectors are formed and applied one at a time (LAPACK dlarfg convention,
-// as in the executor's panel kernels).  Within a CTA, reflector j's update of
-// the A = n-j-1 trailing columns is spread over A groups of Gj lanes (Gj a
-// power of two <= 32, A*Gj <= 256): a group owns one column, its lanes take
-// rows g, g+Gj, ...; the dot products reduce by shuffles inside the group.
-// The group that updates column j+1 also accumulates the squares of its new
-// entries, forms reflector j+1 and scales its vector into the second of two
-// vector buffers, so each reflector costs one block barrier.
+// as in the executor's panel kernels).  The tile lives in registers while it
+// is factored: the CTA's 256 threads form NCOL column groups of G = 256/NCOL
+// adjacent lanes, lane g of column c holding rows g*RPT .. g*RPT+RPT-1 of
+// column c (tile height nb = G*RPT).  Reflector j's vector u is published in
+// shared memory; every column c > j computes its dot product with u from
+// registers, reduces it across its G lanes by shuffles, and updates its
+// registers.  For GEQRT u carries the implicit unit at row j and zeros above
+// it, so the same code updates R's row j; for TSQRT R's row j lives in shared
+// memory (packed) and lane 0 of each column adds and updates it.  The group of
+// column j+1 forms reflector j+1 right after its own update and publishes u
+// in the second of two buffers: one block barrier per reflector.  Tiles move
+// between global memory and registers through a shared staging tile
+// (coalesced global loads and stores).
 #include "tqr_internal.h"
 #include "../../include/tqr.h"
 
@@ -33,8 +39,6 @@ namespace tqr {
 
 namespace {
 
-constexpr int kTs1Threads = 256;
-
 __device__ __forceinline__ void ts1_status(int32_t* status, int code) { atomicCAS(status, 0, code); }
 
 template <typename Real>
@@ -43,171 +47,254 @@ __device__ __forceinline__ Real group_sum(Real x, int G, unsigned gmask) {
     return x;
 }
 
-// Reflector mapping (alpha, x) to (beta, 0): beta = -sign(alpha) ||(alpha, x)||
-// with sign(0) = +1, tau = (beta - alpha) / beta, v = x / (alpha - beta);
-// x = 0 gives tau = 0 and a zero vector.  sig = ||x||^2.  Writes beta over
-// alpha and returns the scale 1 / (alpha - beta).
-template <typename Real>
-__device__ Real make_reflector(Real* ap, Real sig, Real* tau_out, int32_t* status) {
-    const Real alpha = *ap;
-    Real tau = Real(0), scale = Real(0);
-    if (sig != Real(0) || !isfinite(sig)) {
-        const Real nrm = sqrt(fma(alpha, alpha, sig));
-        if (!isfinite(nrm)) ts1_status(status, TQR_ERR_NONFINITE);
-        const Real beta = alpha >= Real(0) ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        scale = Real(1) / (alpha - beta);
-        *ap = beta;
-    }
-    *tau_out = tau;
-    return scale;
-}
-
 __device__ __forceinline__ int packed(int j, int c) { return c * (c + 1) / 2 + j; }
 
-template <typename Real, int NCOL>
-__global__ void __launch_bounds__(kTs1Threads) ts1_kernel(const Ts1Desc* __restrict__ descs, Real* tau_ge,
-                                                           Real* tau_el, int32_t* status) {
+// Shared-memory geometry of one (Real, NCOL, RPT) instantiation.
+template <typename Real, int NCOL, int RPT, int NT>
+struct Ts1Geom {
+    static constexpr int G = NT / NCOL;                     // lanes per column
+    static constexpr int H = G * RPT;                       // tile height nb
+    static constexpr int VPAD = 16 / sizeof(Real);          // one 16-byte slot between lane chunks
+    static constexpr int UCH = RPT + VPAD;                  // chunk stride of a published vector
+    static constexpr int ULEN = G * UCH;                    // one published vector
+    static constexpr int LD = NCOL + 1;                     // staging tile row stride
+    static constexpr int ELEMS = 2 * ULEN + H * LD + NCOL * (NCOL + 1) / 2;
+};
+
+template <typename Real> struct Vec2;
+template <> struct Vec2<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec2<double> { using T = double2; static constexpr int N = 2; };
+
+template <typename Real, int RPT>
+__device__ __forceinline__ Real dot_chunk(const Real* __restrict__ u, const Real (&x)[RPT]) {
+    using V = typename Vec2<Real>::T;
+    constexpr int N = Vec2<Real>::N;
+    Real a[4] = {Real(0), Real(0), Real(0), Real(0)};     // four independent chains
+#pragma unroll
+    for (int k = 0; k < RPT; k += N) {
+        const V w = *reinterpret_cast<const V*>(u + k);
+        if constexpr (N == 4) {
+            a[0] = fma(w.x, x[k], a[0]);
+            a[1] = fma(w.y, x[k + 1], a[1]);
+            a[2] = fma(w.z, x[k + 2], a[2]);
+            a[3] = fma(w.w, x[k + 3], a[3]);
+        } else {
+            a[(k / 2) & 1 ? 2 : 0] = fma(w.x, x[k], a[(k / 2) & 1 ? 2 : 0]);
+            a[(k / 2) & 1 ? 3 : 1] = fma(w.y, x[k + 1], a[(k / 2) & 1 ? 3 : 1]);
+        }
+    }
+    return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+template <typename Real, int RPT>
+__device__ __forceinline__ void axpy_chunk(const Real* __restrict__ u, Real wt, Real (&x)[RPT]) {
+    using V = typename Vec2<Real>::T;
+    constexpr int N = Vec2<Real>::N;
+#pragma unroll
+    for (int k = 0; k < RPT; k += N) {
+        const V w = *reinterpret_cast<const V*>(u + k);
+        if constexpr (N == 4) {
+            x[k] = fma(-w.x, wt, x[k]);
+            x[k + 1] = fma(-w.y, wt, x[k + 1]);
+            x[k + 2] = fma(-w.z, wt, x[k + 2]);
+            x[k + 3] = fma(-w.w, wt, x[k + 3]);
+        } else {
+            x[k] = fma(-w.x, wt, x[k]);
+            x[k + 1] = fma(-w.y, wt, x[k + 1]);
+        }
+    }
+}
+
+// Forms reflector jn from column jn, held by the G lanes of its group (lane
+// g has rows r0..r0+RPT-1 in x).  LAPACK convention: beta = -sign(alpha)
+// ||(alpha, x)|| with sign(0) = +1, tau = (beta - alpha)/beta, v = x/(alpha -
+// beta); x = 0 gives tau = 0 and v = 0.  GEQRT: alpha is row jn of the tile and
+// x its rows below; the published u is (0 above jn, 1 at jn, v below).
+// TSQRT: alpha is R(jn,jn) and x the whole tile column; u = v.
+template <typename Real, int RPT>
+__device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, unsigned gmask, Real (&x)[RPT],
+                                         Real* __restrict__ u, Real* R, Real* s_tau, Real* tau_out,
+                                         int32_t* status) {
+    Real sig = Real(0), a = ge ? Real(0) : R[packed(jn, jn)];   // TS: read before lane 0 overwrites it
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int row = r0 + k;
+        if (!ge || row > jn) sig = fma(x[k], x[k], sig);
+        if (ge && row == jn) a = x[k];
+    }
+    sig = group_sum(sig, G, gmask);
+    if (ge) a = group_sum(a, G, gmask);
+    Real tau = Real(0), scale = Real(0), beta = a;
+    if (sig != Real(0) || !isfinite(sig)) {
+        const Real nrm = sqrt(fma(a, a, sig));
+        beta = a >= Real(0) ? -nrm : nrm;
+        tau = (beta - a) / beta;
+        scale = Real(1) / (a - beta);
+    }
+    if (g == 0) {
+        if (!isfinite(beta)) ts1_status(status, TQR_ERR_NONFINITE);
+        *s_tau = tau;
+        *tau_out = tau;
+        if (!ge) R[packed(jn, jn)] = beta;
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int row = r0 + k;
+        if (ge) {
+            if (row > jn) {
+                x[k] *= scale;
+                u[k] = x[k];
+            } else if (row == jn) {
+                x[k] = beta;
+                u[k] = Real(1);
+            } else {
+                u[k] = Real(0);
+            }
+        } else {
+            x[k] *= scale;
+            u[k] = x[k];
+        }
+    }
+}
+
+template <typename Real, int NCOL, int RPT, int NT>
+__global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ descs, Real* tau_ge, Real* tau_el,
+                                                  int32_t* status) {
+    using Geo = Ts1Geom<Real, NCOL, RPT, NT>;
+    constexpr int G = Geo::G, H = Geo::H, LD = Geo::LD, UCH = Geo::UCH, ULEN = Geo::ULEN;
     extern __shared__ __align__(16) unsigned char ts1_raw[];
-    constexpr int ld = NCOL + 1;
     __shared__ Real s_tau[2];
+    Real* Ub = reinterpret_cast<Real*>(ts1_raw);   // 2 published vectors (16-byte aligned chunks)
+    Real* T = Ub + 2 * ULEN;                       // staging tile: H x LD, row-major
+    Real* R = T + H * LD;                          // packed upper triangle of R
     const Ts1Desc d = descs[blockIdx.x];
-    const int n = d.n, h = d.h;
+    const int n = d.n;
     const int64_t m = d.m;
     Real* A = static_cast<Real*>(d.A);
-    Real* T = reinterpret_cast<Real*>(ts1_raw);   // tile: h x ld, row-major
-    Real* R = T + h * ld;                         // packed upper triangle, NCOL (NCOL+1)/2
-    Real* Vb = R + NCOL * (NCOL + 1) / 2;         // two reflector vectors of h entries
     const int t = threadIdx.x;
+    const int c = t / G, g = t % G;
     const int lane = t & 31;
-    const int p = static_cast<int>((m + h - 1) / h);
+    const int leader = lane & ~(G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << leader);
+    const int r0 = g * RPT;
+    const int p = static_cast<int>((m + H - 1) / H);
+    Real x[RPT];
 
     for (int tile = 0; tile < p; ++tile) {
         const bool ge = tile == 0;
-        const int64_t row0 = static_cast<int64_t>(tile) * h;
-        const int rows = static_cast<int>(m - row0 < h ? m - row0 : h);
-        Real* tau_out = (ge ? tau_ge : tau_el) + d.tau_off + static_cast<int64_t>(tile) * h;
+        const int64_t row0 = static_cast<int64_t>(tile) * H;
+        const int rows = static_cast<int>(m - row0 < H ? m - row0 : H);
+        Real* tau_out = (ge ? tau_ge : tau_el) + d.tau_off + static_cast<int64_t>(tile) * H;
         __syncthreads();
-        for (int e = t; e < rows * n; e += kTs1Threads) {
-            const int r = e % rows, c = e / rows;
-            T[r * ld + c] = A[row0 + r + static_cast<int64_t>(c) * m];
+        for (int e = t; e < H * n; e += NT) {
+            const int r = e % H, cc = e / H;
+            T[r * LD + cc] = r < rows ? A[row0 + r + static_cast<int64_t>(cc) * m] : Real(0);
         }
-        for (int j = n + t; j < h; j += kTs1Threads) tau_out[j] = Real(0);   // padded columns
+        for (int j = n + t; j < H; j += NT) tau_out[j] = Real(0);   // padded columns
         __syncthreads();
-
-        // Reflector 0 by warp 0.
-        if (t < 32) {
-            const int lo = ge ? 1 : 0;
-            Real s = Real(0);
-            for (int r = lo + lane; r < rows; r += 32) s = fma(T[r * ld], T[r * ld], s);
-            s = group_sum(s, 32, 0xffffffffu);
-            Real scale = Real(0);
-            if (lane == 0) {
-                scale = make_reflector(ge ? &T[0] : &R[0], s, &s_tau[0], status);
-                tau_out[0] = s_tau[0];
-            }
-            scale = __shfl_sync(0xffffffffu, scale, 0);
-            for (int r = lo + lane; r < rows; r += 32) {
-                const Real x = T[r * ld] * scale;
-                T[r * ld] = x;
-                Vb[r] = x;
-            }
-        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) x[k] = c < n ? T[(r0 + k) * LD + c] : Real(0);
+        if (c == 0) ts1_form<Real, RPT>(ge, 0, r0, g, G, gmask, x, Ub + g * UCH, R, &s_tau[0], &tau_out[0], status);
         __syncthreads();
 
         for (int j = 0; j < n - 1; ++j) {
-            const int Acols = n - j - 1;
-            int Gj = kTs1Threads / Acols;
-            Gj = Gj >= 32 ? 32 : (Gj >= 16 ? 16 : (Gj >= 8 ? 8 : (Gj >= 4 ? 4 : (Gj >= 2 ? 2 : 1))));
-            if (t < Acols * Gj) {
-                const Real* v = Vb + (j & 1) * h;
-                Real* vn = Vb + ((j + 1) & 1) * h;
+            if (c > j && c < n) {
+                const Real* u = Ub + (j & 1) * ULEN + g * UCH;
                 const Real tau = s_tau[j & 1];
-                const int c = j + 1 + t / Gj, g = t % Gj;
-                const int leader = lane & ~(Gj - 1);
-                const unsigned gmask = (Gj == 32) ? 0xffffffffu : (((1u << Gj) - 1u) << leader);
-                const int lo = ge ? j + 1 : 0;
-                Real* rp = ge ? &T[j * ld + c] : &R[packed(j, c)];
-                Real acc = Real(0);
-                for (int r = lo + g; r < rows; r += Gj) acc = fma(v[r], T[r * ld + c], acc);
-                if (g == 0) acc += *rp;
-                acc = group_sum(acc, Gj, gmask);
+                Real acc = dot_chunk<Real, RPT>(u, x);
+                if (!ge && g == 0) acc += R[packed(j, c)];
+                acc = group_sum(acc, G, gmask);
                 const Real wt = tau * acc;
-                if (g == 0) *rp -= wt;
-                const bool next = c == j + 1;
-                const int nlo = ge ? j + 2 : 0;
-                Real s = Real(0);
-                for (int r = lo + g; r < rows; r += Gj) {
-                    const Real x = fma(-v[r], wt, T[r * ld + c]);
-                    T[r * ld + c] = x;
-                    if (next && r >= nlo) s = fma(x, x, s);
-                }
-                if (next) {                 // the whole group owns column j+1
-                    s = group_sum(s, Gj, gmask);
-                    Real scale = Real(0);
-                    if (g == 0) {
-                        Real* ap = ge ? &T[(j + 1) * ld + (j + 1)] : &R[packed(j + 1, j + 1)];
-                        scale = make_reflector(ap, s, &s_tau[(j + 1) & 1], status);
-                        tau_out[j + 1] = s_tau[(j + 1) & 1];
-                    }
-                    scale = __shfl_sync(gmask, scale, leader);
-                    for (int r = lo + g; r < rows; r += Gj) {
-                        if (r < nlo) continue;
-                        const Real x = T[r * ld + c] * scale;
-                        T[r * ld + c] = x;
-                        vn[r] = x;
-                    }
-                }
+                axpy_chunk<Real, RPT>(u, wt, x);
+                if (!ge && g == 0) R[packed(j, c)] -= wt;
+                if (c == j + 1)
+                    ts1_form<Real, RPT>(ge, j + 1, r0, g, G, gmask, x, Ub + ((j + 1) & 1) * ULEN + g * UCH, R,
+                                        &s_tau[(j + 1) & 1], &tau_out[j + 1], status);
             }
             __syncthreads();
         }
 
+        if (c < n) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) T[(r0 + k) * LD + c] = x[k];
+        }
+        __syncthreads();
         if (ge) {                                  // R = upper triangle of the factored first tile
-            for (int e = t; e < n * (n + 1) / 2; e += kTs1Threads) {
-                int c = 0;
-                while ((c + 1) * (c + 2) / 2 <= e) ++c;
-                const int j = e - c * (c + 1) / 2;
-                R[e] = T[j * ld + c];
+            for (int e = t; e < n * (n + 1) / 2; e += NT) {
+                int cc = 0;
+                while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
+                const int j = e - cc * (cc + 1) / 2;
+                R[e] = T[j * LD + cc];
             }
         }
-        for (int e = t; e < rows * n; e += kTs1Threads) {
-            const int r = e % rows, c = e / rows;
-            A[row0 + r + static_cast<int64_t>(c) * m] = T[r * ld + c];
+        for (int e = t; e < rows * n; e += NT) {
+            const int r = e % rows, cc = e / rows;
+            A[row0 + r + static_cast<int64_t>(cc) * m] = T[r * LD + cc];
         }
     }
     __syncthreads();
     if (p > 1) {                                   // final R over the first tile's upper triangle
-        for (int e = t; e < n * (n + 1) / 2; e += kTs1Threads) {
-            int c = 0;
-            while ((c + 1) * (c + 2) / 2 <= e) ++c;
-            const int j = e - c * (c + 1) / 2;
-            A[j + static_cast<int64_t>(c) * m] = R[e];
+        for (int e = t; e < n * (n + 1) / 2; e += NT) {
+            int cc = 0;
+            while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
+            const int j = e - cc * (cc + 1) / 2;
+            A[j + static_cast<int64_t>(cc) * m] = R[e];
         }
     }
 }
 
-template <typename Real, int NCOL>
-cudaError_t launch_class(const Ts1Desc* d, int count, int hmax, void* tau_ge, void* tau_el, int32_t* status,
-                         cudaStream_t s) {
-    const int smem = ts1_smem_bytes(NCOL, hmax, sizeof(Real));
-    cudaError_t e = cudaFuncSetAttribute(ts1_kernel<Real, NCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <typename Real, int NCOL, int NT, int H>
+cudaError_t launch_one(const Ts1Desc* d, int count, void* tau_ge, void* tau_el, int32_t* status, cudaStream_t s) {
+    constexpr int RPT = H * NCOL / NT;
+    const int smem = Ts1Geom<Real, NCOL, RPT, NT>::ELEMS * static_cast<int>(sizeof(Real));
+    auto* k = ts1_kernel<Real, NCOL, RPT, NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    ts1_kernel<Real, NCOL><<<count, kTs1Threads, smem, s>>>(d, static_cast<Real*>(tau_ge),
-                                                             static_cast<Real*>(tau_el), status);
+    k<<<count, NT, smem, s>>>(d, static_cast<Real*>(tau_ge), static_cast<Real*>(tau_el), status);
     return cudaGetLastError();
+}
+
+// Threads per CTA: 256 for FP32; 512 for FP64, whose DFMA pipe needs more
+// warps in flight.  A thread holds RPT = nb * NCOL / NT rows of its column.
+constexpr int threads_for(int esz) { return esz == 4 ? 256 : 512; }
+
+// Instantiated (column class, tile height) pairs.
+template <typename Real>
+cudaError_t launch_typed(const Ts1Desc* d, int count, int ncol, int h, void* tg, void* te, int32_t* st,
+                         cudaStream_t s) {
+    constexpr int NT = threads_for(sizeof(Real));
+    switch (ncol * 1000 + h) {
+        case 32064: return launch_one<Real, 32, NT, 64>(d, count, tg, te, st, s);
+        case 32128: return launch_one<Real, 32, NT, 128>(d, count, tg, te, st, s);
+        case 32256: return launch_one<Real, 32, NT, 256>(d, count, tg, te, st, s);
+        case 64064: return launch_one<Real, 64, NT, 64>(d, count, tg, te, st, s);
+        case 64128: return launch_one<Real, 64, NT, 128>(d, count, tg, te, st, s);
+        case 64256: return launch_one<Real, 64, NT, 256>(d, count, tg, te, st, s);
+        case 128128: return launch_one<Real, 128, NT, 128>(d, count, tg, te, st, s);
+        case 128256:
+            if constexpr (sizeof(Real) == 4) return launch_one<Real, 128, NT, 256>(d, count, tg, te, st, s);
+            return cudaErrorInvalidValue;                        // 64 FP64 rows per thread would spill
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int geom_elems(int ncol, int h, int esz) {
+    const int G = threads_for(esz) / ncol, rpt = h / G, vpad = 16 / esz;
+    return 2 * G * (rpt + vpad) + h * (ncol + 1) + ncol * (ncol + 1) / 2;
 }
 
 }  // namespace
 
 int ts1_ncol_class(int64_t n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : 0)); }
 
-int ts1_smem_bytes(int ncol_class, int hmax, int elem_size) {
-    return (hmax * (ncol_class + 1) + ncol_class * (ncol_class + 1) / 2 + 2 * hmax) * elem_size;
-}
+int ts1_smem_bytes(int ncol_class, int h, int elem_size) { return geom_elems(ncol_class, h, elem_size) * elem_size; }
 
 bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size) {
     const int cls = ts1_ncol_class(n);
-    if (cls == 0 || n > nb || m < n || nb < 8 || nb > 256) return false;
+    if (cls == 0 || n > nb || m < n) return false;
+    if (nb != 64 && nb != 128 && nb != 256) return false;
+    if (nb < cls) return false;
+    if (cls == 128 && nb == 256 && elem_size == 8) return false;    // would need 64 FP64 rows per thread
     int optin = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -215,18 +302,11 @@ bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size) {
     return ts1_smem_bytes(cls, nb, elem_size) <= optin;
 }
 
-cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int hmax, bool f32, void* tau_ge, void* tau_el,
+cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int h, bool f32, void* tau_ge, void* tau_el,
                        int32_t* status, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    switch (ncol_class) {
-        case 32: return f32 ? launch_class<float, 32>(d, count, hmax, tau_ge, tau_el, status, s)
-                            : launch_class<double, 32>(d, count, hmax, tau_ge, tau_el, status, s);
-        case 64: return f32 ? launch_class<float, 64>(d, count, hmax, tau_ge, tau_el, status, s)
-                            : launch_class<double, 64>(d, count, hmax, tau_ge, tau_el, status, s);
-        case 128: return f32 ? launch_class<float, 128>(d, count, hmax, tau_ge, tau_el, status, s)
-                             : launch_class<double, 128>(d, count, hmax, tau_ge, tau_el, status, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return f32 ? launch_typed<float>(d, count, ncol_class, h, tau_ge, tau_el, status, s)
+               : launch_typed<double>(d, count, ncol_class, h, tau_ge, tau_el, status, s);
 }
 
 }  // namespace tqr

@@ -17,7 +17,7 @@ def test_candidates_cover_square_tiles_and_one_column():
         if tree == tqr.PLASMA:
             assert BS <= -(-512 // nb)
     assert [x[0] for x in autotune.candidates_f32(128)] == [128, 256]
-    assert [x[0] for x in autotune.candidates_f32(32)] == [32, 64, 128, 256]
+    assert [x[0] for x in autotune.candidates_f32(32)] == [64, 128, 256]
 
 
 def test_database_roundtrip_and_lookup(tmp_path):

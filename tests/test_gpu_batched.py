@@ -87,7 +87,7 @@ def test_batched_relaunch_and_cuda_graph():
 from oracle import FLAT_TS as O_FLAT_TS
 from oracle import kernels as oK
 
-ONE_COLUMN = [(300, 32, 64), (1000, 64, 64), (517, 100, 128), (64, 64, 64), (70, 48, 64), (500, 1, 32),
+ONE_COLUMN = [(300, 32, 64), (1000, 64, 64), (517, 100, 128), (64, 64, 64), (70, 48, 64), (500, 1, 64),
               (1200, 128, 128), (40, 32, 256), (2000, 64, 256), (777, 33, 64), (129, 96, 128)]
 
 
