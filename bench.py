@@ -35,6 +35,13 @@ SEED = 1
 # FP64 peak from unit counts: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 CPU_SAMPLE_QS = (1, 2)
+# DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the q = 8 launch of this sweep
+# (5.600 GB for 1.3174e11 flop).  The traffic comes from re-staging reflector
+# blocks and strips per update task, so it grows with the number of strip
+# tasks, i.e. in proportion to the flops at fixed nb and ib; the sweep's
+# per-step traffic is this ratio times the sweep's flops.
+TRAFFIC_BYTES_PER_FLOP = 5.600e9 / 1.3174e11
 
 
 def flops(m, n):
@@ -312,7 +319,11 @@ def gpu_main(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": args.traffic if args.traffic is not None
+                         else TRAFFIC_BYTES_PER_FLOP * workload_flops(),
+                         "traffic_unit": "bytes per step (7 launches), scaled from the q = 8 capture",
+                         "algorithmic_bytes": sum(16.0 * M * NB * q for q in QS),
                          "kernel": "exec_kernel<4> (persistent executor; events around each tqr_factor)",
                          "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)"},
             "cpu_baseline": cpu,

@@ -115,13 +115,15 @@ template <typename Real, int RPT>
 __device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, unsigned gmask, Real (&x)[RPT],
                                          Real* __restrict__ u, Real* R, Real* s_tau, Real* tau_out,
                                          int32_t* status) {
-    Real sig = Real(0), a = ge ? Real(0) : R[packed(jn, jn)];   // TS: read before lane 0 overwrites it
+    Real a = ge ? Real(0) : R[packed(jn, jn)];   // TS: read before lane 0 overwrites it
+    Real sq[4] = {Real(0), Real(0), Real(0), Real(0)};   // four independent chains
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int row = r0 + k;
-        if (!ge || row > jn) sig = fma(x[k], x[k], sig);
+        if (!ge || row > jn) sq[k & 3] = fma(x[k], x[k], sq[k & 3]);
         if (ge && row == jn) a = x[k];
     }
+    Real sig = (sq[0] + sq[1]) + (sq[2] + sq[3]);
     sig = group_sum(sig, G, gmask);
     if (ge) a = group_sum(a, G, gmask);
     Real tau = Real(0), scale = Real(0), beta = a;
@@ -254,32 +256,42 @@ cudaError_t launch_one(const Ts1Desc* d, int count, void* tau_ge, void* tau_el, 
     return cudaGetLastError();
 }
 
-// Threads per CTA: 256 for FP32; 512 for FP64, whose DFMA pipe needs more
-// warps in flight.  A thread holds RPT = nb * NCOL / NT rows of its column.
-constexpr int threads_for(int esz) { return esz == 4 ? 256 : 512; }
+// Threads per CTA: enough that a thread holds at most 32 FP32 or 16 FP64 rows
+// of its column (RPT = nb * NCOL / NT), so that the reflector chain of one
+// matrix has many warps to hide its latency; at least 256 (FP32) / 512 (FP64),
+// at most 1024.
+constexpr int threads_for(int esz, int ncol, int h) {
+    const int want = h * ncol / (esz == 4 ? 32 : 16);
+    const int lo = esz == 4 ? 256 : 512;
+    return want < lo ? lo : (want > 1024 ? 1024 : want);
+}
 
 // Instantiated (column class, tile height) pairs.
+template <typename Real, int NCOL, int H>
+cudaError_t launch_nt(const Ts1Desc* d, int count, void* tg, void* te, int32_t* st, cudaStream_t s) {
+    return launch_one<Real, NCOL, threads_for(sizeof(Real), NCOL, H), H>(d, count, tg, te, st, s);
+}
+
 template <typename Real>
 cudaError_t launch_typed(const Ts1Desc* d, int count, int ncol, int h, void* tg, void* te, int32_t* st,
                          cudaStream_t s) {
-    constexpr int NT = threads_for(sizeof(Real));
     switch (ncol * 1000 + h) {
-        case 32064: return launch_one<Real, 32, NT, 64>(d, count, tg, te, st, s);
-        case 32128: return launch_one<Real, 32, NT, 128>(d, count, tg, te, st, s);
-        case 32256: return launch_one<Real, 32, NT, 256>(d, count, tg, te, st, s);
-        case 64064: return launch_one<Real, 64, NT, 64>(d, count, tg, te, st, s);
-        case 64128: return launch_one<Real, 64, NT, 128>(d, count, tg, te, st, s);
-        case 64256: return launch_one<Real, 64, NT, 256>(d, count, tg, te, st, s);
-        case 128128: return launch_one<Real, 128, NT, 128>(d, count, tg, te, st, s);
+        case 32064: return launch_nt<Real, 32, 64>(d, count, tg, te, st, s);
+        case 32128: return launch_nt<Real, 32, 128>(d, count, tg, te, st, s);
+        case 32256: return launch_nt<Real, 32, 256>(d, count, tg, te, st, s);
+        case 64064: return launch_nt<Real, 64, 64>(d, count, tg, te, st, s);
+        case 64128: return launch_nt<Real, 64, 128>(d, count, tg, te, st, s);
+        case 64256: return launch_nt<Real, 64, 256>(d, count, tg, te, st, s);
+        case 128128: return launch_nt<Real, 128, 128>(d, count, tg, te, st, s);
         case 128256:
-            if constexpr (sizeof(Real) == 4) return launch_one<Real, 128, NT, 256>(d, count, tg, te, st, s);
-            return cudaErrorInvalidValue;                        // 64 FP64 rows per thread would spill
+            if constexpr (sizeof(Real) == 4) return launch_nt<Real, 128, 256>(d, count, tg, te, st, s);
+            return cudaErrorInvalidValue;                        // 32 FP64 rows per thread at 1024 threads
         default: return cudaErrorInvalidValue;
     }
 }
 
 int geom_elems(int ncol, int h, int esz) {
-    const int G = threads_for(esz) / ncol, rpt = h / G, vpad = 16 / esz;
+    const int G = threads_for(esz, ncol, h) / ncol, rpt = h / G, vpad = 16 / esz;
     return 2 * G * (rpt + vpad) + h * (ncol + 1) + ncol * (ncol + 1) / 2;
 }
 
