@@ -52,6 +52,22 @@ def workload_flops(qs=QS):
     return sum(flops(M, NB * q) for q in qs)
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """Largest x over all ranks (x itself without a process group): the
+    job's time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank, world, seconds):
+    """Whole-job throughput of N independent replicas: all ranks' units / job time."""
+    return units_per_rank * world / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -252,12 +268,8 @@ def gpu_main(args):
         if rc != 0:
             raise RuntimeError("device status %d (%s) at q=%d" % (rc, tqr.tqr_strerror(rc), q))
     timed_launches = launches
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    total_flops = workload_flops() * args.steps * world
-    value = total_flops / elapsed / 1e9
+    elapsed = max_over_ranks(elapsed, dist)
+    value = weak_value(workload_flops() * args.steps, world, elapsed) / 1e9
 
     per_q = {}
     for q, e0, e1 in kt:
@@ -302,11 +314,8 @@ def gpu_main(args):
             e2e_step()
             torch.cuda.synchronize()
             tsum += time.perf_counter() - t_s
-        if dist:
-            t = torch.tensor([tsum], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tsum = float(t.item())
-        e2e = {"value": workload_flops() * args.e2e_steps * world / tsum / 1e9, "unit": "GFLOP/s",
+        tsum = max_over_ranks(tsum, dist)
+        e2e = {"value": weak_value(workload_flops() * args.e2e_steps, world, tsum) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": args.e2e_steps,
                "api": "tqr_factor_host (pinned host A in, R and V out)"}
         for h in e2e_handles.values():

@@ -262,3 +262,59 @@ def test_timeout_is_reported_and_context_survives():
     F = otq.factor(A, 64, 16, tqr.GREEDY)
     compare(tqr.to_numpy(At), F.A, np.abs(F.r()).max(), tol_for(A), "R and V after timeout")
     f.free()
+
+
+# ------------------------------------------------------------ degenerate cases
+def _degenerate(case):
+    rng = np.random.default_rng(21)
+    if case == "zero":
+        return np.zeros((300, 130)), 32, 8
+    if case == "zero_column":
+        A = rng.standard_normal((300, 130))
+        A[:, 40] = 0.0                                  # inside the second tile column
+        A[:, 64] = 0.0                                  # first column of the third tile column
+        return A, 32, 8
+    if case == "identity":
+        return np.eye(256, 128), 32, 8
+    if case == "one_by_one":
+        return np.array([[3.0]]), 8, 4
+    if case == "column_vector":
+        return rng.standard_normal((1000, 1)), 64, 16
+    if case == "rank_deficient":
+        return rng.standard_normal((400, 12)) @ rng.standard_normal((12, 96)), 32, 8
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["zero", "zero_column", "identity", "one_by_one", "column_vector",
+                                  "rank_deficient"])
+@pytest.mark.parametrize("tree", [tqr.GREEDY, tqr.FLAT_TS])
+def test_degenerate_inputs(case, tree):
+    """Zero reflectors (x = 0 gives tau = 0 and a zero tail, LAPACK's
+    convention), a 1 x 1 matrix, a single column and a rank-deficient matrix:
+    R and V against the oracle, and A = QR with orthogonal Q."""
+    A, nb, ib = _degenerate(case)
+    f, Aout = gpu_factor(A, nb, ib, tree)
+    assert tqr.tqr_sync(f) == 0
+    F = otq.factor(A, nb, ib, tree)
+    m, n = A.shape
+    if case in ("zero", "identity", "one_by_one"):
+        assert np.array_equal(Aout, F.A)                 # no rounding happens at all
+    else:
+        scale = np.abs(F.r()).max()
+        if case == "rank_deficient":
+            # The first 12 columns are independent: R's leading 12 rows are determined
+            # as for A[:, :12]; the trailing rows are rounding noise.
+            compare(np.triu(Aout[:12, :n]), np.triu(F.A[:12, :n]), scale, tol_for(A[:, :12]), "leading R rows")
+        elif case == "zero_column":
+            # Zero columns give identity reflectors; the rest is as well determined as
+            # the matrix without them.
+            keep = [c for c in range(n) if c not in (40, 64)]
+            compare(Aout, F.A, scale, tol_for(A[:, keep]), "R and V")
+        else:
+            compare(Aout, F.A, scale, tol_for(A), "R and V")
+    if case == "zero":
+        Q = gpu_q_explicit(f, m, n)
+        assert np.array_equal(Q, np.eye(m, n))           # every reflector is the identity
+    else:
+        check_targets(f, A, Aout)
+    f.free()
