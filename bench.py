@@ -587,9 +587,16 @@ def costmodel_main(args):
     from paper_1104_4475_gb300 import build, costmodel
     build.build()
     torch.cuda.set_device(0)
-    path = args.cost_data or os.path.join(ROOT, "paper_1104_4475_gb300", "data", "costmodel_timings_gb300.csv")
+    data_dir = os.path.join(ROOT, "paper_1104_4475_gb300", "data")
+    path = args.cost_data or os.path.join(data_dir, "costmodel_timings_gb300.csv")
+    heldout = os.path.join(data_dir, "costmodel_heldout_gb300.csv")
     recs = costmodel.load_records(path)
-    train, test = costmodel.split(recs)
+    if args.cost_data is None and os.path.exists(heldout):
+        train = recs                                            # 100 training shapes; 200 held-out shapes,
+        test = costmodel.disjoint(train, costmodel.load_records(heldout))   # minus any (m, n) seen in training
+        recs = recs + test
+    else:
+        train, test = costmodel.split(recs)
     X, y = costmodel.design(train)
     steps = 3000
     costmodel.train(X[:64], y[:64], steps=10)                # warm-up (build, first launches)
@@ -607,7 +614,8 @@ def costmodel_main(args):
     line = {"metric": "cost-model pick makespan / exhaustive best (held-out shapes, FP64)",
             "value": fp64["model_over_best"], "unit": "x", "n_gpus": 1, "steps": steps, "warmup": 10,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "executor timings on GB300 (%d runs, %d shapes)" % (len(recs), len(costmodel.by_shape(recs))),
+            "data": "executor timings on GB300 (%d runs; %d training shapes, %d held-out shapes)"
+                    % (len(recs), len(costmodel.by_shape(train)), len(costmodel.by_shape(test))),
             "config": {"workload": "3-layer MLP (width 64, FP32), full-batch Adam on %d training runs; m in "
                                    "[4096,65536], n in [256,m], at most 5e11 flop per run; 12 FP64 and 6 "
                                    "split-TF32 candidates per shape" % len(train)},

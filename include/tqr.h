@@ -184,6 +184,20 @@ int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream);
 int tqr_set_trace(tqr_factors* f, int enable);
 int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count);
 
+/* Dependency edges (u -> v: v may start only after u has finished) of the
+ * handle's factorization graph, in the device task numbering of
+ * tqr_get_trace; host only.  With a trace, every edge must satisfy
+ * end(u) <= start(v) (a happens-before check of the executor).  cap in edges,
+ * *count = number of edges (TQR_ERR_CAPACITY if cap is too small). */
+int tqr_get_edges(const tqr_factors* f, int32_t* src, int32_t* dst, int64_t cap, int64_t* count);
+
+/* Test instrument: fills the handle's workspace -- tau arrays, and the FP32
+ * T and V arrays of a low-precision handle -- with NaN on the handle's stream.
+ * A following factorization with the handle reads those entries only after
+ * the tasks that write them have run, so its results stay finite and equal
+ * to an unpoisoned run's; a read before the write shows up as NaN. */
+int tqr_poison_workspace(tqr_factors* f);
+
 /* Waits for the handle's last enqueued work and returns its device status:
  * TQR_OK, TQR_ERR_TIMEOUT, TQR_ERR_NONFINITE or TQR_ERR_CUDA. */
 int tqr_sync(tqr_factors* f);

@@ -76,7 +76,7 @@ def random_shapes(count, seed, m_range=(4096, 65536), n_range=(256, 8192), max_f
     return out
 
 
-def collect(shapes, with_lp=True, log=None, seed=1):
+def collect(shapes, with_lp=True, log=None, seed=1, out=None):
     """Time every candidate configuration on each shape with CUDA events
     around tqr_factor_ex (the second of two runs, so the cached plan is
     reused as in steady use); returns a list of records."""
@@ -103,6 +103,8 @@ def collect(shapes, with_lp=True, log=None, seed=1):
                          "seconds": secs})
         if log:
             log("shape %d/%d (%d x %d) done" % (si + 1, len(shapes), m, n))
+        if out:
+            save_records(recs, out)                    # after every shape: a cut-off run keeps its data
         del src, work
     return recs
 
@@ -225,6 +227,12 @@ def evaluate(model, recs, prec=0):
     return rows
 
 
+def disjoint(train, test):
+    """The test records whose (m, n) does not occur in the training records."""
+    seen = {(r["m"], r["n"]) for r in train}
+    return [r for r in test if (r["m"], r["n"]) not in seen]
+
+
 def split(recs, holdout_frac=0.25, seed=0):
     shapes = sorted(by_shape(recs))
     rng = np.random.default_rng(seed)
@@ -250,17 +258,18 @@ def main(argv=None):
     c.add_argument("--out", required=True)
     e = sub.add_parser("evaluate")
     e.add_argument("--data", required=True)
+    e.add_argument("--heldout", default=None, help="separate held-out timings (train on all of --data)")
     e.add_argument("--steps", type=int, default=3000)
     e.add_argument("--model-out", default=None)
     a = ap.parse_args(argv)
     if a.cmd == "collect":
         t0 = time.time()
-        recs = collect(random_shapes(a.shapes, a.seed), log=lambda s: print(s, file=sys.stderr, flush=True))
-        save_records(recs, a.out)
+        recs = collect(random_shapes(a.shapes, a.seed), log=lambda s: print(s, file=sys.stderr, flush=True),
+                       out=a.out)
         print(json.dumps({"records": len(recs), "seconds": time.time() - t0}))
     else:
         recs = load_records(a.data)
-        tr, te = split(recs)
+        tr, te = (recs, disjoint(recs, load_records(a.heldout))) if a.heldout else split(recs)
         X, y = design(tr)
         model, losses = train(X, y, steps=a.steps)
         Xt, yt = design(te)

@@ -563,6 +563,45 @@ int tqr_set_trace(tqr_factors* f, int enable) {
     return TQR_OK;
 }
 
+int tqr_get_edges(const tqr_factors* f, int32_t* src, int32_t* dst, int64_t cap, int64_t* count) {
+    try {
+        if (!f || !f->plan) return -1;
+        if (!count) return -5;
+        const Graph& g = f->plan->g;
+        const int64_t ne = static_cast<int64_t>(g.succ.size());
+        *count = ne;
+        if (cap < ne) return TQR_ERR_CAPACITY;
+        if ((!src || !dst) && ne > 0) return -2;
+        int64_t e = 0;
+        for (size_t u = 0; u + 1 < g.succ_ptr.size(); ++u)
+            for (int32_t k = g.succ_ptr[u]; k < g.succ_ptr[u + 1]; ++k, ++e) {
+                src[e] = static_cast<int32_t>(u);
+                dst[e] = g.succ[k];
+            }
+        return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_poison_workspace(tqr_factors* f) {
+    if (!f || !f->plan) return -1;
+    const Plan& P = *f->plan;
+    const size_t ntau = static_cast<size_t>(P.p) * P.q * P.key.nb;
+    const size_t nt = static_cast<size_t>(P.p) * P.q * P.key.ib * P.key.nb;
+    const size_t nv = static_cast<size_t>(P.p) * P.q * P.key.nb * P.key.nb;
+    // All-ones bytes are a NaN in both FP64 and FP32.
+    if (cudaMemsetAsync(f->tau_ge, 0xff, ntau * sizeof(double), f->stream) != cudaSuccess ||
+        cudaMemsetAsync(f->tau_el, 0xff, ntau * sizeof(double), f->stream) != cudaSuccess)
+        return TQR_ERR_CUDA;
+    if (f->T_ge && (cudaMemsetAsync(f->T_ge, 0xff, nt * sizeof(float), f->stream) != cudaSuccess ||
+                    cudaMemsetAsync(f->T_el, 0xff, nt * sizeof(float), f->stream) != cudaSuccess ||
+                    cudaMemsetAsync(f->V_ge, 0xff, nv * sizeof(float), f->stream) != cudaSuccess ||
+                    cudaMemsetAsync(f->V_el, 0xff, nv * sizeof(float), f->stream) != cudaSuccess))
+        return TQR_ERR_CUDA;
+    return TQR_OK;
+}
+
 int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count) {
     try {
         if (!f || !f->plan) return -1;

@@ -99,6 +99,8 @@ def lib():
             "tqr_batch_sync": [vp],
             "tqr_factor_batched_f32": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, vp, ctypes.POINTER(vp)],
             "tqr_batch_tau": [vp, i32, vp, vp],
+            "tqr_get_edges": [vp, pi32, pi32, i64, pi64],
+            "tqr_poison_workspace": [vp],
             "tqr_mlp_param_count": [i32],
             "tqr_mlp_forward": [vp, i32, vp, i32, vp, vp],
             "tqr_mlp_loss_grad": [vp, i32, vp, vp, i32, vp, vp, vp, vp],
@@ -434,6 +436,24 @@ def tqr_get_trace(f):
     _check(lib().tqr_get_trace(ctypes.c_void_p(f.ptr), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                out.shape[0], ctypes.byref(cnt)), "tqr_get_trace")
     return out[: cnt.value]
+
+
+def tqr_get_edges(f):
+    """(edges, 2) int32: (u, v) dependency edges of the factorization graph."""
+    cnt = ctypes.c_int64(0)
+    rc = lib().tqr_get_edges(ctypes.c_void_p(f.ptr), None, None, 0, ctypes.byref(cnt))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_get_edges")
+    src = np.zeros(max(1, cnt.value), dtype=np.int32)
+    dst = np.zeros(max(1, cnt.value), dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().tqr_get_edges(ctypes.c_void_p(f.ptr), src.ctypes.data_as(P), dst.ctypes.data_as(P), src.shape[0],
+                               ctypes.byref(cnt)), "tqr_get_edges")
+    return np.stack([src[: cnt.value], dst[: cnt.value]], axis=1)
+
+
+def tqr_poison_workspace(f):
+    _check(lib().tqr_poison_workspace(ctypes.c_void_p(f.ptr)), "tqr_poison_workspace")
 
 
 def tqr_sync(f, raise_on_error=True):

@@ -58,3 +58,14 @@ def producer_violations(trace):
             if key not in end or s < end[key]:
                 bad.append((kind, i, piv, k, js))
     return bad
+
+
+def edge_violations(trace, edges):
+    """Dependency edges (u, v) of the graph whose task v started before task u
+    ended -- the happens-before check of a traced run (empty when the
+    executor honoured every edge)."""
+    if len(edges) == 0:
+        return []
+    u, v = edges[:, 0], edges[:, 1]
+    bad = trace[v, 5] < trace[u, 6]
+    return [tuple(e) for e in edges[bad].tolist()]

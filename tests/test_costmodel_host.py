@@ -56,6 +56,19 @@ def test_stored_timings_and_split():
     assert costmodel.split(recs)[1] == te               # deterministic
 
 
+def test_stored_heldout_timings():
+    recs = costmodel.load_records(DATA.replace("costmodel_timings_gb300", "costmodel_heldout_gb300"))
+    shapes = costmodel.by_shape(recs)
+    assert len(recs) == 3600 and len(shapes) == 200
+    train = {(r["m"], r["n"]) for r in costmodel.load_records(DATA)}
+    held = {(r["m"], r["n"]) for r in recs}
+    assert len(held & train) <= 5                        # different seeds: almost disjoint shapes
+    kept = costmodel.disjoint(costmodel.load_records(DATA), recs)
+    assert not {(r["m"], r["n"]) for r in kept} & train and len(costmodel.by_shape(kept)) >= 195
+    for rs in shapes.values():
+        assert len(rs) == 18 and all(r["seconds"] > 0 for r in rs)
+
+
 def test_records_roundtrip(tmp_path):
     recs = [{"shape": 0, "m": 4096, "n": 256, "nb": 128, "ib": 32, "tree": 5, "BS": 1, "prec": 0,
              "seconds": 0.0125}]

@@ -189,3 +189,34 @@ def test_fp32_batch_rejects_unsupported():
     B = torch.zeros(300, 64, dtype=torch.float32, device="cuda").t().contiguous().t()
     with pytest.raises(tqr.TqrError):
         tqr.tqr_factor_batched_f32([B], 32)               # n > nb
+
+
+def test_one_column_degenerate_inputs():
+    """Zero matrices and zero columns through the one-column kernel, FP64 and
+    FP32: identity reflectors (tau = 0) leave them exactly as the oracle does."""
+    rng = np.random.default_rng(3)
+    Z = np.zeros((500, 48))
+    C = rng.standard_normal((700, 64))
+    C[:, 5] = 0.0
+    mats = [Z, C, np.eye(128, 96)]
+    nbs = [64, 128, 128]
+    As = [tqr.colmajor(A) for A in mats]
+    b = tqr.tqr_factor_batched(As, nbs, 8, tqr.FLAT_TS, 1)
+    assert tqr.tqr_batch_sync(b) == 0 and b.info()["n_fused"] == 3
+    for A, At, nb in zip(mats, As, nbs):
+        F = otq.factor(A, nb, 8, O_FLAT_TS)
+        got = tqr.to_numpy(At)
+        if A is C:
+            keep = [c for c in range(64) if c != 5]
+            tol = 8 * np.linalg.cond(A[:, keep]) * A.shape[0] * U
+            assert np.abs(got - F.A).max() / np.abs(F.r()).max() <= tol
+        else:
+            assert np.array_equal(got, F.A)
+    b.free()
+    Z32 = [torch.zeros(96, 400, dtype=torch.float32, device="cuda").t()]
+    b = tqr.tqr_factor_batched_f32(Z32, 128)
+    assert tqr.tqr_batch_sync(b) == 0
+    assert torch.count_nonzero(Z32[0]).item() == 0
+    tg, te = tqr.tqr_batch_tau(b, 0, 400, 96, 128, f32=True)
+    assert not tg.any() and not te.any()
+    b.free()

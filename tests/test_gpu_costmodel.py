@@ -112,16 +112,16 @@ def test_training_fits_smooth_function(tqr):
 
 
 def test_trained_model_gains_over_fixed_configuration(tqr):
-    """Trained on executor timings of 75 shapes (GB300, one factorization per
-    configuration), the network's pick on the 25 held-out shapes is within 2 %
-    of the exhaustive best on average, and better than both the fixed default
-    (Greedy, nb 256) and the smallest-critical-path rule."""
+    """Trained on executor timings of 100 shapes (GB300, 18 configurations
+    each), the network's pick on 200 other shapes (timed the same way) is
+    within 2 % of the exhaustive best on average, and better than both the
+    fixed default (Greedy, nb 256) and the smallest-critical-path rule."""
     import os
     from paper_1104_4475_gb300 import costmodel
-    path = os.path.join(os.path.dirname(costmodel.__file__), "data", "costmodel_timings_gb300.csv")
-    recs = costmodel.load_records(path)
-    train, test = costmodel.split(recs)
-    assert len(costmodel.by_shape(test)) == 25
+    data = os.path.join(os.path.dirname(costmodel.__file__), "data")
+    train = costmodel.load_records(os.path.join(data, "costmodel_timings_gb300.csv"))
+    test = costmodel.disjoint(train, costmodel.load_records(os.path.join(data, "costmodel_heldout_gb300.csv")))
+    assert len(costmodel.by_shape(test)) >= 195
     X, y = costmodel.design(train)
     model, losses = costmodel.train(X, y, steps=3000)
     assert losses[-1][1] < 0.01 * losses[0][1]

@@ -39,8 +39,32 @@ def test_trace_rows_and_producer_order(tree, BS, prec, tmp_path):
     assert np.all(tr[:, 7] < torch.cuda.get_device_properties(0).multi_processor_count)
     assert set(tr[:, 0].tolist()) <= set(range(6))
     assert ttrace.producer_violations(tr) == []
+    edges = tqr.tqr_get_edges(g)
+    assert len(edges) == info["n_edges"]
+    assert ttrace.edge_violations(tr, edges) == []           # happens-before on every edge
     s = ttrace.summary(tr)
     assert 0.0 < s["busy_fraction"] <= 1.0 and s["tasks"] == len(tr)
     doc = ttrace.to_chrome(tr, str(tmp_path / "t.json"))
     assert len(doc["traceEvents"]) == len(tr)
     g.free()
+
+
+@pytest.mark.parametrize("prec", [tqr.TQR_FP64, tqr.TQR_SPLIT_TF32])
+def test_poisoned_workspace_is_never_read_before_written(prec):
+    """NaN in every tau / T / V entry before a rerun: the rerun's result is
+    bit-identical to the clean run and finite, so no task read workspace that
+    its producers had not written yet."""
+    A0 = workloads.uniform(1500, 640, seed=8)               # ragged: 12 x 5 tiles of 128
+    At = tqr.colmajor(A0)
+    f = tqr.tqr_factor_ex(At, 128, 32, tqr.GREEDY, 1, prec)
+    assert tqr.tqr_sync(f) == 0
+    clean = tqr.to_numpy(At)
+    for _ in range(2):
+        tqr.tqr_poison_workspace(f)
+        At2 = tqr.colmajor(A0)
+        g = tqr.tqr_factor_ex(At2, 128, 32, tqr.GREEDY, 1, prec, reuse=f)
+        assert g is f and tqr.tqr_sync(f) == 0
+        out = tqr.to_numpy(At2)
+        assert np.isfinite(out).all()
+        assert np.array_equal(out, clean)
+    f.free()

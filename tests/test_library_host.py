@@ -168,3 +168,26 @@ def test_argument_errors():
     with pytest.raises(tqr.TqrError):
         tqr.tqr_critical_path(4, 2, 99)
     assert tqr.tqr_strerror(tqr.TQR_ERR_TIMEOUT) == "device wait timed out"
+
+
+def test_factor_argument_errors_before_any_device_work():
+    """Argument checks of the factorization entry points run on the host
+    before any CUDA call, so they are testable without a GPU."""
+    L = tqr.lib()
+    ct = tqr.tqr.ctypes
+    fake = ct.c_void_p(0x1000)                            # never dereferenced: rejected earlier
+    out = ct.c_void_p(None)
+    # tqr_factor(A, m, n, nb, ib, tree, BS, stream, out)
+    assert L.tqr_factor(None, 64, 32, 32, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -1
+    assert L.tqr_factor(fake, 0, 32, 32, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -2
+    assert L.tqr_factor(fake, 64, 65, 32, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -3     # n > m
+    assert L.tqr_factor(fake, 64, 32, 30, 5, tqr.GREEDY, 1, None, ct.byref(out)) == -4     # nb % 4
+    assert L.tqr_factor(fake, 64, 32, 32, 12, tqr.GREEDY, 1, None, ct.byref(out)) == -5    # ib does not divide nb
+    assert L.tqr_factor(fake, 64, 32, 32, 8, 42, 1, None, ct.byref(out)) == -6             # unknown tree
+    assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.PLASMA, 0, None, ct.byref(out)) == -7     # BS < 1
+    assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.PLASMA_TS, 3, None, ct.byref(out)) == -7  # BS > p = 2
+    assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.GRASAP, 2, None, ct.byref(out)) == -7     # k > q = 1
+    assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.GREEDY, 1, None, None) == -9
+    # tqr_factor_ex(..., precision, stream, out)
+    assert L.tqr_factor_ex(fake, 64, 32, 32, 8, tqr.GREEDY, 1, 7, None, ct.byref(out)) == -8
+    assert out.value is None
