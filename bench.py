@@ -2,11 +2,13 @@
 
 Workload ("tree sweep"): m = 16384 (p = 64 tile rows), nb = 256, ib = 32,
 n = 256 q for q in {1, 2, 4, 8, 16, 32, 64}, entries iid U[-0.5, 0.5]
-(seed 1), Greedy tree (TT kernels).  One step factors all seven matrices;
-flops = sum of 2 n^2 (m - n/3) (the LAPACK count).  Inputs are resident in
-HBM; each step first restores the seven matrices from pristine copies
-(device-to-device, 8.5 GB of traffic) after writing a 256 MiB buffer to
-flush L2, and both are inside the timed region.
+(seed 1), the elimination tree of each q chosen by a per-tree sweep
+(Greedy for small q, Fibonacci at q = 16, PlasmaTree with TS kernels inside
+domains at q >= 32).  One step factors all seven matrices; flops = sum of
+2 n^2 (m - n/3) (the LAPACK count).  Inputs are resident in HBM; each step
+first restores the seven matrices from pristine copies (device-to-device,
+8.5 GB of traffic) after writing a 256 MiB buffer to flush L2, and both are
+inside the timed region.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 instead (numpy, the machine's host cores) on a bounded sample of the same
@@ -30,7 +32,13 @@ sys.path.insert(0, ROOT)
 
 M, NB, IB = 16384, 256, 32
 QS = (1, 2, 4, 8, 16, 32, 64)
-TREE_NAME = "Greedy"
+# Tree (and PlasmaTree domain size) per q: the fastest of every tree, with BS
+# over {2, 4, 8, 16}, in a per-tree sweep of this workload on GB300 (ties go to
+# Greedy); the paper's experiments likewise keep the best domain size.
+SWEEP_TREES = {1: ("greedy", 1), 2: ("greedy", 1), 4: ("greedy", 1), 8: ("greedy", 1), 16: ("fibonacci", 1),
+               32: ("plasma_ts", 16), 64: ("plasma_ts", 16)}
+TREE_NAME = "tuned per q: " + ", ".join("q=%d %s%s" % (q, t, "(BS=%d)" % b if t.startswith("plasma") else "")
+                                        for q, (t, b) in SWEEP_TREES.items())
 SEED = 1
 # FP64 peak from unit counts: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
@@ -186,7 +194,7 @@ def reference_main(args):
 
 def config_dict():
     return {"workload": "FP64 tree sweep: m=16384 (p=64), nb=256, ib=32, n=256q for q in "
-                        "{1,2,4,8,16,32,64}, U[-0.5,0.5] entries, Greedy tree (TT kernels)",
+                        "{1,2,4,8,16,32,64}, U[-0.5,0.5] entries, tree autotuned per q",
             "m": M, "nb": NB, "ib": IB, "q": list(QS), "tree": TREE_NAME, "parallelism": "replicas",
             "l2": "256 MiB flush write + input restore (8.5 GB D2D) each step, inside the timed region"}
 
@@ -231,7 +239,8 @@ def gpu_main(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            handles[q] = tqr.tqr_factor(work[q], NB, IB, tqr.GREEDY, 1, stream=stream, reuse=handles.get(q))
+            tree, bs = SWEEP_TREES[q]
+            handles[q] = tqr.tqr_factor(work[q], NB, IB, tqr.TREES[tree], bs, stream=stream, reuse=handles.get(q))
             launches += 2                               # init + executor
             if kernel_times is not None:
                 e1.record(stream)
@@ -292,7 +301,8 @@ def gpu_main(args):
         def e2e_step():
             for q in QS:
                 a = hosts[q].numpy().T                      # Fortran view of pinned memory
-                e2e_handles[q] = tqr.tqr_factor_host(a, NB, IB, tqr.GREEDY, 1, stream=stream,
+                tree, bs = SWEEP_TREES[q]
+                e2e_handles[q] = tqr.tqr_factor_host(a, NB, IB, tqr.TREES[tree], bs, stream=stream,
                                                      reuse=e2e_handles.get(q))
 
         # The host inputs are refilled from a host copy before each step (outside the timing).
@@ -331,7 +341,8 @@ def gpu_main(args):
                          "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": args.traffic if args.traffic is not None
                          else TRAFFIC_BYTES_PER_FLOP * workload_flops(),
-                         "traffic_unit": "bytes per step (7 launches), scaled from the q = 8 capture",
+                         "traffic_unit": "bytes per step (7 launches), estimated from the DRAM bytes per "
+                                         "flop of an ncu capture of the Greedy q = 8 launch",
                          "algorithmic_bytes": sum(16.0 * M * NB * q for q in QS),
                          "kernel": "exec_kernel<4> (persistent executor; events around each tqr_factor)",
                          "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)"},
@@ -352,6 +363,11 @@ def gpu_main(args):
 
 # ----------------------------------------------------- mixed-precision LS
 LS_M, LS_N, LS_NB, LS_IB = 65536, 4096, 256, 32
+# Tree for both arithmetic paths: PlasmaTree with TS kernels inside domains of
+# 32 tile rows was the fastest of Greedy, Fibonacci, BinaryTree, ASAP,
+# PlasmaTree and PlasmaTree-TS (BS 4..128) for this shape in FP64 and in
+# split-TF32 on GB300.
+LS_TREE, LS_BS = "plasma_ts", 32
 LS_KAPPAS = (1e2, 1e6, 1e10)
 
 
@@ -377,7 +393,7 @@ def lstsq_main(args):
                 x = torch.zeros(LS_N, dtype=torch.float64, device="cuda")
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                info = tqr.tqr_lstsq(A, b, x, LS_NB, LS_IB, tqr.GREEDY, 1, prec, tol, maxit)
+                info = tqr.tqr_lstsq(A, b, x, LS_NB, LS_IB, tqr.TREES[LS_TREE], LS_BS, prec, tol, maxit)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 if rep > 0:
@@ -408,7 +424,7 @@ def lstsq_main(args):
             "vs_baseline": None, "dtype": "f64+tf32x3", "data": "synthetic",
             "config": {"workload": "least squares A = U diag(sigma) V^T, m=65536, n=4096, sigma log-spaced "
                                    "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
-                       "nb": LS_NB, "ib": LS_IB, "tree": "Greedy", "kappas": list(LS_KAPPAS)},
+                       "nb": LS_NB, "ib": LS_IB, "tree": "PlasmaTree-TS(BS=%d)" % LS_BS, "kappas": list(LS_KAPPAS)},
             "detail": detail}
     print(json.dumps(line), flush=True)
     return 0

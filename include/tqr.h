@@ -13,8 +13,9 @@
  *  - Return value: 0 (TQR_OK) on success.  A negative value -k in -1..-99
  *    means that argument k (1-based) is invalid.  Named codes below.
  *  - No C++ exception crosses this boundary.
- *  - Matrices are column-major FP64.  "device" pointers are CUDA global
- *    memory of the current device; "host" pointers are ordinary host memory.
+ *  - Matrices are column-major FP64 (FP32 for tqr_factor_batched_f32 and the
+ *    cost-model network).  "device" pointers are CUDA global memory of the
+ *    current device; "host" pointers are ordinary host memory.
  *  - Device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
  *    default stream) and returns before it completes.  Errors detected on the
  *    device (timeout, non-finite values) surface at tqr_sync().
