@@ -363,11 +363,11 @@ def gpu_main(args):
 
 # ----------------------------------------------------- mixed-precision LS
 LS_M, LS_N, LS_NB, LS_IB = 65536, 4096, 256, 32
-# Tree for both arithmetic paths: PlasmaTree with TS kernels inside domains of
-# 32 tile rows was the fastest of Greedy, Fibonacci, BinaryTree, ASAP,
-# PlasmaTree and PlasmaTree-TS (BS 4..128) for this shape in FP64 and in
-# split-TF32 on GB300.
-LS_TREE, LS_BS = "plasma_ts", 32
+# Tree for both arithmetic paths: Greedy.  PlasmaTree with TS kernels inside
+# domains of 32 tile rows factors this shape 5-7 % faster on GB300, but its
+# flat TS chains make c = Q^T b slower, and the whole mixed-precision solve
+# took 0.526 s against 0.492 s with Greedy.
+LS_TREE, LS_BS = "greedy", 1
 LS_KAPPAS = (1e2, 1e6, 1e10)
 
 
@@ -424,7 +424,7 @@ def lstsq_main(args):
             "vs_baseline": None, "dtype": "f64+tf32x3", "data": "synthetic",
             "config": {"workload": "least squares A = U diag(sigma) V^T, m=65536, n=4096, sigma log-spaced "
                                    "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
-                       "nb": LS_NB, "ib": LS_IB, "tree": "PlasmaTree-TS(BS=%d)" % LS_BS, "kappas": list(LS_KAPPAS)},
+                       "nb": LS_NB, "ib": LS_IB, "tree": "%s(BS=%d)" % (LS_TREE, LS_BS), "kappas": list(LS_KAPPAS)},
             "detail": detail}
     print(json.dumps(line), flush=True)
     return 0

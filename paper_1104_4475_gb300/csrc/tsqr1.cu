@@ -7,7 +7,7 @@
 // and there are no update tasks.  When thousands of such matrices are
 // factored together the parallelism comes from the batch, so one CTA runs the
 // whole chain of one matrix and keeps R resident in shared memory; the tiles
-// below it stream through shared memory once (read, reflect, write back V).
+// below it are read once, reflected in registers and written back as V.
 // The results are those of tqr_factor(A, m, n, nb, ib, TQR_FLAT_TS, ...):
 // R in the upper triangle of rows 0..n-1, GEQRT's V below the diagonal of tile
 // row 1, TSQRT's V in the whole of every other tile row, tau per reflector in
@@ -16,9 +16,10 @@
 //
 // Reflectors are formed and applied one at a time (LAPACK dlarfg convention,
 // as in the executor's panel kernels).  The tile lives in registers while it
-// is factored: the CTA's 256 threads form NCOL column groups of G = 256/NCOL
+// is factored: the CTA's NT threads form NCOL column groups of G = NT/NCOL
 // adjacent lanes, lane g of column c holding rows g*RPT .. g*RPT+RPT-1 of
-// column c (tile height nb = G*RPT).  Reflector j's vector u is published in
+// column c (tile height nb = G*RPT; NT chosen so that RPT <= 32 in FP32 and
+// <= 16 in FP64, 256..1024 threads).  Reflector j's vector u is published in
 // shared memory; every column c > j computes its dot product with u from
 // registers, reduces it across its G lanes by shuffles, and updates its
 // registers.  For GEQRT u carries the implicit unit at row j and zeros above
