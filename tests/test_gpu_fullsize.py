@@ -1,20 +1,27 @@
 """Parity at the benchmark's full size and launch configuration (m = 16384,
-nb = 256, ib = 32, Greedy, U[-0.5, 0.5] entries, seed 1 -- the sweep points
-q = 8 and q = 64), where the oracle cannot factor the whole matrix:
+nb = 256, ib = 32, U[-0.5, 0.5] entries, seed 1, and the tree the benchmark
+uses for each q -- the sweep points q = 8, 16 and 64), where the oracle
+cannot factor the whole matrix:
 
 * sampled outputs the oracle computes exactly: the whole first tile column
   (R_11 and every reflector of column 1) comes only from column-1 kernels,
-  whose elimination list Greedy does not change with q, so it must equal the
-  oracle's factorization of A[:, :nb] element-wise;
+  whose elimination list does not change with q for these trees, so it must
+  equal the oracle's factorization of A[:, :nb] element-wise;
 * properties that hold at any size: ||R[:, c]|| = ||A[:, c]|| for every
   column c (Q is orthogonal), ||Q^T b|| = ||b||, and on sampled columns
   A[:, c] = Q R[:, c] and Q[:, S]^T Q[:, S] = I.
 """
 
+import os
+import sys
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402  (the benchmark's tree per q)
 
 from oracle import tiled_qr as otq
 import paper_1104_4475_gb300 as tqr
@@ -34,16 +41,18 @@ def cuda():
     build.build()
 
 
-@pytest.mark.parametrize("q", [8, 64])
-def test_full_size_greedy(q):
+@pytest.mark.parametrize("q", [8, 16, 64])
+def test_full_size_bench_configuration(q):
     n = NB * q
+    name, BS = bench.SWEEP_TREES[q]
+    tree = tqr.TREES[name]
     A = workloads.sweep_config(q)               # the benchmark's input for this q
     At = tqr.colmajor(A)
-    f = tqr.tqr_factor(At, NB, IB, tqr.GREEDY)
+    f = tqr.tqr_factor(At, NB, IB, tree, BS)
     tqr.tqr_sync(f)
     # Sampled outputs: the first tile column against the oracle.
     A1 = np.ascontiguousarray(A[:, :NB])
-    F1 = otq.factor(A1, NB, IB, tqr.GREEDY)
+    F1 = otq.factor(A1, NB, IB, tree, BS)
     col1 = tqr.to_numpy(At[:, :NB])
     tol = max(1e-13, 8 * np.linalg.cond(A1) * M * U)
     err = np.abs(col1 - F1.A).max() / np.abs(F1.r()).max()
