@@ -42,6 +42,8 @@ TREE_NAME = "tuned per q: " + ", ".join("q=%d %s%s" % (q, t, "(BS=%d)" % b if t.
 SEED = 1
 # FP64 peak from unit counts: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# FP32 (FFMA) peak from unit counts: 152 SMs x 128 FMA/clk/SM (256 flop) x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12
 CPU_SAMPLE_QS = (1, 2)
 # DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the q = 8 launch of this sweep
@@ -522,6 +524,12 @@ def batched_main(args):
             "config": {"workload": "4096 FP64 matrices, m ~ U[512,16384], n in {32,64,128}, N(0,1); one "
                                    "persistent launch replayed from a CUDA graph; step = input restore + replay",
                        "count": BT_COUNT, "flops_per_step": flops},
+            "roofline": {"bound": "alu", "achieved": tuned["kernel_gflops"] / 1e3, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": tuned["kernel_gflops"] / 1e3 / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "batch graph (one-column FlatTree-TS kernel + executor), FP64",
+                         "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)",
+                         "fp32_frac": fp32["kernel_gflops"] / 1e3 / FP32_PEAK_TFLOPS,
+                         "fp32_peak": FP32_PEAK_TFLOPS},
             "detail": {"tuned": tuned, "fixed_nb64_ib16_greedy": fixed, "fp32_tuned": fp32,
                        "speedup_tuned_vs_fixed": tuned["gflops"] / fixed["gflops"],
                        "tuning_seconds": t_tune,
