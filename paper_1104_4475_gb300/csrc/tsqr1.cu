@@ -18,8 +18,8 @@
 // as in the executor's panel kernels).  The tile lives in registers while it
 // is factored: the CTA's NT threads form NCOL column groups of G = NT/NCOL
 // adjacent lanes, lane g of column c holding rows g*RPT .. g*RPT+RPT-1 of
-// column c (tile height nb = G*RPT; NT chosen so that RPT <= 16, 256..1024
-// threads).  Reflector j's vector u is published in
+// column c (tile height nb = G*RPT; NT chosen so that RPT <= 16 in FP32 and
+// <= 8 in FP64 where 1024 threads allow it).  Reflector j's vector u is published in
 // shared memory; every column c > j computes its dot product with u from
 // registers, reduces it across its G lanes by shuffles, and updates its
 // registers.  For GEQRT u carries the implicit unit at row j and zeros above
@@ -257,11 +257,12 @@ cudaError_t launch_one(const Ts1Desc* d, int count, void* tau_ge, void* tau_el, 
     return cudaGetLastError();
 }
 
-// Threads per CTA: enough that a thread holds at most 16 rows of its column
-// (RPT = nb * NCOL / NT), so that the reflector chain of one matrix has many
-// warps to hide its latency; at least 256 (FP32) / 512 (FP64), at most 1024.
+// Threads per CTA: enough that a thread holds at most 16 FP32 / 8 FP64 rows of
+// its column (RPT = nb * NCOL / NT), so that the reflector chain of one matrix
+// has many warps to hide its latency; at least 256 (FP32) / 512 (FP64), at
+// most 1024.
 constexpr int threads_for(int esz, int ncol, int h) {
-    const int want = h * ncol / 16;
+    const int want = h * ncol / (esz == 4 ? 16 : 8);
     const int lo = esz == 4 ? 256 : 512;
     return want < lo ? lo : (want > 1024 ? 1024 : want);
 }
