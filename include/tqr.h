@@ -130,7 +130,10 @@ typedef struct {
  *         same (m, n, nb, ib, tree, BS), its device buffers are reused and
  *         nothing is allocated; otherwise a new handle is created (the old
  *         one is left untouched).  Set *out = NULL before the first call.
- * Errors: -1..-9 argument errors, TQR_ERR_NOMEM, TQR_ERR_CUDA.
+ * Errors: -1..-9 argument errors, TQR_ERR_NOMEM, TQR_ERR_CUDA, and
+ * TQR_ERR_CAPACITY when the task graph could exceed 2e9 device tasks
+ * (p q (q+1) (nb/8+1) >= 2e9, e.g. 65536 x 65536 with nb = 16), checked
+ * before anything is built.
  * ------------------------------------------------------------------------- */
 int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
                void* stream, tqr_factors** out);

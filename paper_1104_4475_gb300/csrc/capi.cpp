@@ -99,11 +99,20 @@ static double lapack_flops(int64_t m, int64_t n) {
     return 2.0 * N * N * (M - N / 3.0);
 }
 
+// Upper bound of the device tasks of a factorization graph: at most q tile
+// tasks per elimination and tile (p q of them), each update split into at
+// most nb / 8 + 1 strips.  Task ids are int32 on the device.
+static bool plan_fits(int64_t p, int64_t q, int nb) {
+    const double bound = static_cast<double>(p) * q * (q + 1) * (nb / 8 + 1);
+    return bound < 2.0e9;
+}
+
 static int make_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
     auto P = std::make_shared<Plan>();
     P->key = key;
     P->p = static_cast<int>((key.m + key.nb - 1) / key.nb);
     P->q = static_cast<int>((key.n + key.nb - 1) / key.nb);
+    if (!plan_fits(P->p, P->q, key.nb)) return TQR_ERR_CAPACITY;
     P->ts = key.ts;
     if (key.tree >= 0) {
         int rc = make_elims(P->p, P->q, key.tree, key.BS, P->elims);
@@ -423,6 +432,7 @@ static int check_common(double* A, int64_t m, int64_t n, int nb, int ib) {
     if (ib < 1 || ib > 64 || nb % ib != 0) return -5;
     const int64_t p = (m + nb - 1) / nb, q = (n + nb - 1) / nb;
     if (p > 65535 || q > 65535) return -2;
+    if (!plan_fits(p, q, nb)) return TQR_ERR_CAPACITY;
     return TQR_OK;
 }
 
@@ -770,6 +780,7 @@ int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero
         if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -4;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!cp) return -5;
+        if (!plan_fits(p, q, 0)) return TQR_ERR_CAPACITY;   // tile tasks alone would not fit
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
         if (rc != TQR_OK) return rc;
@@ -797,6 +808,7 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
         if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -4;
         if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -4;
         if (!count) return -8;
+        if (!plan_fits(p, q, 0)) return TQR_ERR_CAPACITY;   // tile tasks alone would not fit
         std::vector<Elim> el;
         int rc = make_elims(p, q, tree, BS, el);
         if (rc != TQR_OK) return rc;
@@ -890,7 +902,10 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
         int nbmax = 0, ibmax = 0;
         for (int c = 0; c < count; ++c) {
             const int rc = check_common(A[c], m[c], n[c], nb[c], ib[c]);
-            if (rc != TQR_OK) return rc == -1 ? -2 : (rc == -2 ? -3 : (rc == -3 ? -4 : (rc == -4 ? -5 : -6)));
+            if (rc != TQR_OK) {
+                if (rc < -99) return rc;                  // named code (capacity)
+                return rc == -1 ? -2 : (rc == -2 ? -3 : (rc == -3 ? -4 : (rc == -4 ? -5 : -6)));
+            }
             if (tree[c] < TQR_FLAT_TS || tree[c] > TQR_PLASMA_TS) return -7;
             const int p = static_cast<int>((m[c] + nb[c] - 1) / nb[c]);
             const int q = static_cast<int>((n[c] + nb[c] - 1) / nb[c]);

@@ -190,4 +190,9 @@ def test_factor_argument_errors_before_any_device_work():
     assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.GREEDY, 1, None, None) == -9
     # tqr_factor_ex(..., precision, stream, out)
     assert L.tqr_factor_ex(fake, 64, 32, 32, 8, tqr.GREEDY, 1, 7, None, ct.byref(out)) == -8
+    # maximum sizes: more than 65535 tile rows, and a task graph beyond int32 task ids
+    assert L.tqr_factor(fake, 65536 * 16 + 16, 32, 16, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -2
+    assert L.tqr_factor(fake, 65536, 65536, 16, 8, tqr.GREEDY, 1, None, ct.byref(out)) == tqr.TQR_ERR_CAPACITY
+    cp = ct.c_int64(0)
+    assert L.tqr_critical_path(4096, 4096, tqr.GREEDY, 1, ct.byref(cp), None) == tqr.TQR_ERR_CAPACITY
     assert out.value is None
