@@ -62,6 +62,18 @@ def workload_flops(qs=QS):
     return sum(flops(M, NB * q) for q in qs)
 
 
+_JSONL = None
+
+
+def emit(line):
+    """Prints the result line; with --jsonl also appends it to that file."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if _JSONL:
+        with open(_JSONL, "a") as fh:
+            fh.write(text + "\n")
+
+
 def max_over_ranks(x, dist=None, device="cuda"):
     """Largest x over all ranks (x itself without a process group): the
     job's time is its slowest rank's."""
@@ -190,7 +202,7 @@ def reference_main(args):
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc()},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -355,7 +367,7 @@ def gpu_main(args):
             "fp64_pct_of_peak": 100.0 * value / 1e3 / FP64_PEAK_TFLOPS / world,
             "detail": detail,
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     for h in handles.values():
         h.free()
     if dist:
@@ -428,7 +440,7 @@ def lstsq_main(args):
                                    "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
                        "nb": LS_NB, "ib": LS_IB, "tree": "%s(BS=%d)" % (LS_TREE, LS_BS), "kappas": list(LS_KAPPAS)},
             "detail": detail}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -535,7 +547,7 @@ def batched_main(args):
                        "tuning_seconds": t_tune,
                        "classes": [{k: c[k] for k in ("n", "m_lo", "m_hi", "nb", "ib", "tree", "BS", "gflops")}
                                    for c in db["classes"]]}}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -597,7 +609,7 @@ def trees_main(args):
                                    "{2,4,8,16}", "l2": "256 MiB flush write before each factorization"},
             "best_tree": max(sweep, key=sweep.get), "sweep_gflops": sweep, "per_tree": out,
             "unit_ms": 1e3 * unit_s, "seconds": time.perf_counter() - t_all}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -646,7 +658,7 @@ def costmodel_main(args):
             "detail": {"fp64": fp64, "split_tf32": lp, "test_rmse_log_seconds": rmse,
                        "train_seconds": train_s, "train_steps_per_s": steps / train_s,
                        "final_train_loss": losses[-1][1]}}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -661,6 +673,7 @@ def main():
                          "batched: 4096 tall-skinny matrices in one launch; trees: the sweep for every tree; "
                          "costmodel: train and score the learned cost model")
     ap.add_argument("--cost-data", default=None, help="executor timings CSV for --workload costmodel")
+    ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--tune-db", default=None, help="autotune database to load, or to write after tuning")
     ap.add_argument("--tune-sample", type=int, default=32, help="matrices per size class when tuning")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -669,6 +682,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per executor launch from an ncu capture (for the roofline line)")
     args = ap.parse_args()
+    global _JSONL
+    _JSONL = args.jsonl
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

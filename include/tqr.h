@@ -180,7 +180,8 @@ int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream);
  * paper's simulator has no device counterpart).  tqr_set_trace(f, 1) makes
  * later factorizations with f record, for every device task, its start and
  * end on the GPU's %globaltimer (ns) and the SM that ran it (allocates
- * 16 bytes per task once).  tqr_get_trace waits for the handle's work and
+ * 16 bytes per task once); with TQR_TRACE set (not "0") in the environment
+ * every new handle starts with tracing on.  tqr_get_trace waits for the handle's work and
  * writes 8 int64 per task to out (host): kind, i, piv, k, j * 65536 + strip,
  * start ns, end ns, SM id -- in device task order; cap in tasks, *count =
  * number of tasks (TQR_ERR_CAPACITY if cap is too small,

@@ -364,10 +364,21 @@ static ExecParams base_params(const tqr_factors* f) {
     return x;
 }
 
+// TQR_TRACE set (and not "0") in the environment: every new handle records
+// per-task traces, as if tqr_set_trace(f, 1) had been called.
+static bool trace_from_env() {
+    static const bool on = [] {
+        const char* e = std::getenv("TQR_TRACE");
+        return e && e[0] && !(e[0] == '0' && e[1] == 0);
+    }();
+    return on;
+}
+
 static int new_handle(const std::shared_ptr<Plan>& plan, tqr_factors** out) {
     tqr_factors* f = new (std::nothrow) tqr_factors();
     if (!f) return TQR_ERR_NOMEM;
     f->plan = plan;
+    f->trace_on = trace_from_env() ? 1 : 0;
     const size_t ntau = static_cast<size_t>(plan->p) * plan->q * plan->key.nb;
     if (cudaMalloc(&f->tau_ge, ntau * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&f->tau_el, ntau * sizeof(double)) != cudaSuccess ||

@@ -133,3 +133,8 @@ def test_trained_model_gains_over_fixed_configuration(tqr):
     m, n = test[0]["m"], test[0]["n"]
     c = costmodel.pick(model, m, n)
     assert c in costmodel.configs_for(m) and c[4] == 0
+    # the trained model saves and reloads (versioned JSON) with identical predictions
+    import json
+    again = costmodel.Model.from_json(json.loads(json.dumps(model.to_json())))
+    Xt, _ = costmodel.design(test[:50])
+    assert np.array_equal(again.predict_log_seconds(Xt), model.predict_log_seconds(Xt))

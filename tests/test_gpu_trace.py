@@ -68,3 +68,23 @@ def test_poisoned_workspace_is_never_read_before_written(prec):
         assert np.isfinite(out).all()
         assert np.array_equal(out, clean)
     f.free()
+
+
+def test_trace_enabled_from_environment():
+    """TQR_TRACE=1 turns tracing on for every new handle (no tqr_set_trace call)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_1104_4475_gb300 as tqr\n"
+            "from paper_1104_4475_gb300 import workloads\n"
+            "A = tqr.colmajor(workloads.uniform(512, 256, seed=3))\n"
+            "f = tqr.tqr_factor(A, 64, 16, tqr.GREEDY); tqr.tqr_sync(f)\n"
+            "tr = tqr.tqr_get_trace(f)\n"
+            "assert tr.shape[0] == f.info()['n_device_tasks'] and (tr[:, 6] >= tr[:, 5]).all()\n"
+            "print('traced', tr.shape[0])\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, TQR_TRACE="1"), capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.startswith("traced")
