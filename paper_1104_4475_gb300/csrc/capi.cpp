@@ -382,6 +382,8 @@ static int new_handle(const std::shared_ptr<Plan>& plan, tqr_factors** out) {
     const size_t ntau = static_cast<size_t>(plan->p) * plan->q * plan->key.nb;
     if (cudaMalloc(&f->tau_ge, ntau * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&f->tau_el, ntau * sizeof(double)) != cudaSuccess ||
+        cudaMemset(f->tau_ge, 0, ntau * sizeof(double)) != cudaSuccess ||     // slots no reflector uses stay 0
+        cudaMemset(f->tau_el, 0, ntau * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&f->status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(f->status, 0, sizeof(int32_t)) != cudaSuccess ||
         alloc_state(f->fst, plan->dg.d.ntasks, f->status) != cudaSuccess) {
@@ -984,6 +986,8 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
         if (upload(&b->d_mats, mats) != cudaSuccess) return TQR_ERR_NOMEM;
         if (cudaMalloc(&b->tau_ge, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
+            cudaMemset(b->tau_ge, 0, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
+            cudaMemset(b->tau_el, 0, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess ||
             (b->has_exec && alloc_state(b->st, b->dg.d.ntasks, b->status) != cudaSuccess))
             return TQR_ERR_NOMEM;
@@ -1044,6 +1048,8 @@ int tqr_factor_batched_f32(int count, float* const* A, const int64_t* m, const i
         }
         if (cudaMalloc(&b->tau_ge, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
+            cudaMemset(b->tau_ge, 0, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
+            cudaMemset(b->tau_el, 0, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess)
             return TQR_ERR_NOMEM;
         if (build_ts1(b, fused) != TQR_OK) return TQR_ERR_NOMEM;

@@ -25,6 +25,7 @@
 #pragma once
 
 #include "tqr_internal.h"
+#include "reflector.cuh"
 #include "../../include/tqr.h"
 
 #include <cuda_runtime.h>
@@ -266,11 +267,9 @@ __device__ void fb_form(const Smem& S, int nb, int j0, int jj, int lane, int32_t
         const double alpha = *ap;
         double tau = 0.0;
         if (sig != 0.0 || !isfinite(sig)) {
-            const double nrm = sqrt(fma(alpha, alpha, sig));
-            if (!isfinite(nrm)) set_status(status, TQR_ERR_NONFINITE);
-            const double beta = alpha >= 0.0 ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
+            double beta;
+            reflector_scalars(alpha, sig, &beta, &tau, &scale);
+            if (!isfinite(beta)) set_status(status, TQR_ERR_NONFINITE);
             *ap = beta;
         }                                   // else x is zero: identity reflector, zero tail
         S.taus[jj] = tau;

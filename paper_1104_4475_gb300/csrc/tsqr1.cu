@@ -30,6 +30,7 @@
 // between global memory and registers through a shared staging tile
 // (coalesced global loads and stores).
 #include "tqr_internal.h"
+#include "reflector.cuh"
 #include "../../include/tqr.h"
 
 #include <cuda_runtime.h>
@@ -128,12 +129,7 @@ __device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, 
     sig = group_sum(sig, G, gmask);
     if (ge) a = group_sum(a, G, gmask);
     Real tau = Real(0), scale = Real(0), beta = a;
-    if (sig != Real(0) || !isfinite(sig)) {
-        const Real nrm = sqrt(fma(a, a, sig));
-        beta = a >= Real(0) ? -nrm : nrm;
-        tau = (beta - a) / beta;
-        scale = Real(1) / (a - beta);
-    }
+    if (sig != Real(0) || !isfinite(sig)) reflector_scalars(a, sig, &beta, &tau, &scale);
     if (g == 0) {
         if (!isfinite(beta)) ts1_status(status, TQR_ERR_NONFINITE);
         *s_tau = tau;
