@@ -47,11 +47,11 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12
 CPU_SAMPLE_QS = (1, 2)
 # DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the q = 8 launch of this sweep
-# (5.600 GB for 1.3174e11 flop).  The traffic comes from re-staging reflector
+# (5.602 GB for 1.3174e11 flop).  The traffic comes from re-staging reflector
 # blocks and strips per update task, so it grows with the number of strip
 # tasks, i.e. in proportion to the flops at fixed nb and ib; the sweep's
 # per-step traffic is this ratio times the sweep's flops.
-TRAFFIC_BYTES_PER_FLOP = 5.600e9 / 1.3174e11
+TRAFFIC_BYTES_PER_FLOP = 5.602e9 / 1.3174e11
 
 
 def flops(m, n):
