@@ -222,6 +222,14 @@ void tqr_free(tqr_factors* f);
 int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
                     double* B_host, int64_t nrhs, void* stream, tqr_factors** out);
 
+/* tqr_factor_host without the final wait: every copy and kernel is enqueued on
+ * `stream` and the call returns; tqr_sync(*out) waits and reports the status.
+ * A_host (and B_host) must stay allocated and unmodified until then; with
+ * pinned host memory the copies run asynchronously, so matrices handled on
+ * different streams overlap their transfers with each other's factorization. */
+int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
+                          double* B_host, int64_t nrhs, void* stream, tqr_factors** out);
+
 /* Least squares min ||A x - b||_2 (Section 1 names least squares as the main
  * use of the factorization).  A: device, m x n (m >= n), column-major, lda = m,
  * left unchanged (the library factors a copy); b: device, m; x: device, n,

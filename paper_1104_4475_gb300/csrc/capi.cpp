@@ -694,8 +694,21 @@ void tqr_free(tqr_factors* f) {
     delete f;
 }
 
+static int factor_host_impl(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
+                            double* B_host, int64_t nrhs, void* stream, tqr_factors** out, bool wait);
+
 int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS, double* B_host,
                     int64_t nrhs, void* stream, tqr_factors** out) {
+    return factor_host_impl(A_host, m, n, nb, ib, tree, BS, B_host, nrhs, stream, out, true);
+}
+
+int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS, double* B_host,
+                          int64_t nrhs, void* stream, tqr_factors** out) {
+    return factor_host_impl(A_host, m, n, nb, ib, tree, BS, B_host, nrhs, stream, out, false);
+}
+
+static int factor_host_impl(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
+                            double* B_host, int64_t nrhs, void* stream, tqr_factors** out, bool wait) {
     try {
         if (!A_host) return -1;
         if (!out) return -11;
@@ -739,7 +752,7 @@ int tqr_factor_host(double* A_host, int64_t m, int64_t n, int nb, int ib, int tr
             cudaSuccess)
             return TQR_ERR_CUDA;
         *out = f;
-        return tqr_sync(f);
+        return wait ? tqr_sync(f) : TQR_OK;
     } catch (...) {
         return TQR_ERR_INTERNAL;
     }

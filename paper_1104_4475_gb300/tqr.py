@@ -89,6 +89,7 @@ def lib():
             "tqr_sync": [vp],
             "tqr_get_info": [vp, ctypes.POINTER(tqr_info)],
             "tqr_factor_host": [vp, i64, i64, i32, i32, i32, i32, vp, i64, vp, ctypes.POINTER(vp)],
+            "tqr_factor_host_async": [vp, i64, i64, i32, i32, i32, i32, vp, i64, vp, ctypes.POINTER(vp)],
             "tqr_elimination_list": [i32, i32, i32, i32, pi32, i64, pi64],
             "tqr_validate_list": [i32, i32, pi32, i64],
             "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
@@ -473,9 +474,12 @@ def tqr_free(f):
     f.free()
 
 
-def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None):
+def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None, wait=True):
     """End to end on host arrays: A (m x n, Fortran-ordered float64 numpy
-    array) is overwritten by R and V; B (m x nrhs, Fortran order) by Q^T B."""
+    array) is overwritten by R and V; B (m x nrhs, Fortran order) by Q^T B.
+    wait=False enqueues everything on `stream` and returns at once
+    (tqr_factor_host_async): call tqr_sync on the result before reading A or
+    B, and keep them alive and unmodified until then."""
     if not (isinstance(A, np.ndarray) and A.dtype == np.float64 and A.flags.f_contiguous):
         raise TypeError("A must be a Fortran-ordered float64 numpy array")
     m, n = A.shape
@@ -485,9 +489,9 @@ def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None):
             raise TypeError("B must be a Fortran-ordered float64 numpy array with m rows")
         bp, nrhs = ctypes.c_void_p(B.ctypes.data), (B.shape[1] if B.ndim == 2 else 1)
     h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
-    rc = lib().tqr_factor_host(ctypes.c_void_p(A.ctypes.data), m, n, nb, ib, int(tree), BS, bp, nrhs,
-                               _stream(stream), ctypes.byref(h))
-    _check(rc, "tqr_factor_host")
+    fn = lib().tqr_factor_host if wait else lib().tqr_factor_host_async
+    rc = fn(ctypes.c_void_p(A.ctypes.data), m, n, nb, ib, int(tree), BS, bp, nrhs, _stream(stream), ctypes.byref(h))
+    _check(rc, "tqr_factor_host" if wait else "tqr_factor_host_async")
     if reuse is not None and h.value == reuse.ptr:
         return reuse
     return Factors(h.value, None)

@@ -318,3 +318,26 @@ def test_degenerate_inputs(case, tree):
     else:
         check_targets(f, A, Aout)
     f.free()
+
+
+def test_host_async_on_two_streams_matches_sync():
+    """tqr_factor_host_async: two matrices enqueued on two streams, then
+    tqr_sync; results equal the synchronous call's bit for bit."""
+    mats = [np.asfortranarray(workloads.gaussian(768, 256, seed=31)),
+            np.asfortranarray(workloads.uniform(1000, 300, seed=32))]
+    want = []
+    for A in mats:
+        a = A.copy(order="F")
+        f = tqr.tqr_factor_host(a, 64, 16, tqr.GREEDY)
+        want.append(a)
+        f.free()
+    pinned = [torch.from_numpy(A.T.copy()).pin_memory() for A in mats]   # row-major view of A^T = A in F order
+    views = [p.numpy().T for p in pinned]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hs = [tqr.tqr_factor_host(v, 64, 16, tqr.GREEDY, stream=s, wait=False) for v, s in zip(views, streams)]
+    for h in hs:
+        assert tqr.tqr_sync(h) == 0
+    for v, w in zip(views, want):
+        assert np.array_equal(v, w)
+    for h in hs:
+        h.free()
