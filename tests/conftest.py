@@ -12,6 +12,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
 
 
+def pytest_collection_modifyitems(config, items):
+    """Run the full-size modules (tens of GB on the device, minutes each)
+    after every small-size test, keeping the order within each group."""
+    def full_size(item):
+        return os.path.basename(str(item.fspath)).startswith("test_gpu_fullsize")
+    items[:] = [it for it in items if not full_size(it)] + [it for it in items if full_size(it)]
+
+
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
