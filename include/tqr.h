@@ -213,6 +213,18 @@ int tqr_get_info(const tqr_factors* f, tqr_info* info);
 /* Releases the handle's device and host memory (synchronizes first). */
 void tqr_free(tqr_factors* f);
 
+/* The library caches one plan (elimination list, task graph on the device,
+ * apply graphs) per distinct (m, n, nb, ib, tree, BS) or caller-given list it
+ * has factored, so that later calls with the same arguments build nothing.
+ * tqr_release_plans drops every cached plan that no live handle uses, frees
+ * its device memory, and clears the host-side plans of batched calls; it
+ * returns the number of device plans dropped (>= 0) or TQR_ERR_INTERNAL.
+ * Live handles keep their own plan and stay valid; a later call with released
+ * arguments rebuilds the plan.  Host entry point: it frees device memory, so
+ * it synchronizes with the device and must not be called during stream
+ * capture. */
+int tqr_release_plans(void);
+
 /* End-to-end convenience for host data: copies A_host (m x n, column-major,
  * leading dimension m) to the device, factors it, and copies A (R and V)
  * back to A_host; if B_host is not NULL it also copies B_host (m x nrhs,

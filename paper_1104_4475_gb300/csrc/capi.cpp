@@ -94,6 +94,15 @@ static bool uses_bs(int tree) { return tree == TQR_PLASMA || tree == TQR_PLASMA_
 // Kernel family recorded in the plan key: 0 TT, 1 TS, 2 TS inside domains.
 static int kernel_mode(int tree) { return tree == TQR_FLAT_TS ? 1 : tree == TQR_PLASMA_TS ? 2 : 0; }
 
+// The plan key of a factorization with a generated tree on device `dev`
+// (Sameh-Kuck lowers to the same TT list as FlatTree).
+static PlanKey tree_key(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int dev) {
+    return PlanKey{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree, uses_bs(tree) ? BS : 0,
+                   kernel_mode(tree), dev, {}};
+}
+
+static bool same_key(const PlanKey& a, const PlanKey& b) { return !(a < b) && !(b < a); }
+
 static double lapack_flops(int64_t m, int64_t n) {
     const double M = static_cast<double>(m), N = static_cast<double>(n);
     return 2.0 * N * N * (M - N / 3.0);
@@ -408,7 +417,10 @@ static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors**
         if (smem > maxsm - 1024) return TQR_ERR_UNSUPPORTED;
     }
     tqr_factors* f = *out;
-    if (!f || f->plan != plan) {
+    if (f && f->plan && same_key(f->plan->key, key)) {
+        f->plan = plan;                       // same graph (the cached copy may have been released)
+    } else {
+        f = nullptr;
         rc = new_handle(plan, &f);
         if (rc != TQR_OK) return rc;
     }
@@ -427,8 +439,11 @@ static int run_factor(const PlanKey& key, double* A, void* stream, tqr_factors**
     f->prec = prec;
     f->stream = static_cast<cudaStream_t>(stream);
     if (f->trace_on && !f->trace) {
-        if (cudaMalloc(&f->trace, 2 * sizeof(uint64_t) * std::max<int32_t>(1, plan->dg.d.ntasks)) != cudaSuccess)
+        if (cudaMalloc(&f->trace, 2 * sizeof(uint64_t) * std::max<int32_t>(1, plan->dg.d.ntasks)) != cudaSuccess) {
+            f->trace = nullptr;
+            if (f != *out) delete f;
             return TQR_ERR_NOMEM;
+        }
     }
     ExecParams P = base_params(f);
     P.trace = f->trace_on ? f->trace : nullptr;
@@ -464,9 +479,7 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
         if (!out) return -9;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
-        PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
-                    uses_bs(tree) ? BS : 0, kernel_mode(tree), dev, {}};
-        return run_factor(key, A, stream, out);
+        return run_factor(tree_key(m, n, nb, ib, tree, BS, dev), A, stream, out);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
     } catch (...) {
@@ -488,9 +501,7 @@ int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int
         if (!out) return -10;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
-        PlanKey key{m, n, nb, ib, tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree,
-                    uses_bs(tree) ? BS : 0, kernel_mode(tree), dev, {}};
-        return run_factor(key, A, stream, out, precision);
+        return run_factor(tree_key(m, n, nb, ib, tree, BS, dev), A, stream, out, precision);
     } catch (const std::bad_alloc&) {
         return TQR_ERR_NOMEM;
     } catch (...) {
@@ -710,13 +721,20 @@ int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, 
 static int factor_host_impl(double* A_host, int64_t m, int64_t n, int nb, int ib, int tree, int BS,
                             double* B_host, int64_t nrhs, void* stream, tqr_factors** out, bool wait) {
     try {
-        if (!A_host) return -1;
+        int rc = check_common(A_host, m, n, nb, ib);     // same argument positions as tqr_factor
+        if (rc != TQR_OK) return rc;
         if (!out) return -11;
         if (B_host && nrhs < 0) return -9;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         tqr_factors* prev = *out;
-        double* dA = prev ? prev->own_A : nullptr;
-        const bool same = prev && prev->plan && prev->plan->key.m == m && prev->plan->key.n == n && dA;
+        // Reuse the previous handle's device copy of A only if tqr_factor will reuse
+        // the handle itself (same plan key); a new handle gets a buffer of its own, so
+        // that the previous handle's data is left untouched.
+        const bool same = prev && prev->plan && prev->own_A &&
+                          same_key(prev->plan->key, tree_key(m, n, nb, ib, tree, BS, dev));
+        double* dA = same ? prev->own_A : nullptr;
         if (!same) {
             if (cudaMalloc(&dA, static_cast<size_t>(m) * n * sizeof(double)) != cudaSuccess) return TQR_ERR_NOMEM;
         }
@@ -724,14 +742,13 @@ static int factor_host_impl(double* A_host, int64_t m, int64_t n, int nb, int ib
             cudaSuccess)
             return TQR_ERR_CUDA;
         tqr_factors* f = same ? prev : nullptr;
-        int rc = tqr_factor(dA, m, n, nb, ib, tree, BS, stream, &f);
+        rc = tqr_factor(dA, m, n, nb, ib, tree, BS, stream, &f);
         if (rc != TQR_OK) {
             if (!same) cudaFree(dA);
             return rc;
         }
-        if (f != prev) {
-            f->own_A = dA;            // new handle adopts the buffer
-        }
+        if (!same) f->own_A = dA;     // the new handle adopts the buffer
+        *out = f;                     // from here on the caller owns f, also on error
         if (B_host && nrhs > 0) {
             const size_t be = static_cast<size_t>(m) * nrhs;
             if (f->own_B_elems < be) {
@@ -751,7 +768,6 @@ static int factor_host_impl(double* A_host, int64_t m, int64_t n, int nb, int ib
         if (cudaMemcpyAsync(A_host, dA, static_cast<size_t>(m) * n * sizeof(double), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess)
             return TQR_ERR_CUDA;
-        *out = f;
         return wait ? tqr_sync(f) : TQR_OK;
     } catch (...) {
         return TQR_ERR_INTERNAL;
@@ -854,6 +870,29 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
             if (finish) finish[t] = fin[t];
         }
         return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
+int tqr_release_plans(void) {
+    try {
+        int dropped = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_plans_mu);
+            auto& mp = plans();
+            for (auto it = mp.begin(); it != mp.end();) {
+                if (it->second.use_count() == 1) {      // held by the cache alone
+                    it = mp.erase(it);
+                    ++dropped;
+                } else {
+                    ++it;
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_hplans_mu);
+        hplans().clear();                               // batches copy what they use
+        return dropped;
     } catch (...) {
         return TQR_ERR_INTERNAL;
     }

@@ -124,6 +124,8 @@ def lib():
         L.tqr_batch_free.restype = None
         L.tqr_free.argtypes = [vp]
         L.tqr_free.restype = None
+        L.tqr_release_plans.argtypes = []
+        L.tqr_release_plans.restype = ctypes.c_int
         L.tqr_strerror.argtypes = [ctypes.c_int]
         L.tqr_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -474,6 +476,14 @@ def tqr_free(f):
     f.free()
 
 
+def tqr_release_plans():
+    """Drop the cached plans no live handle uses; returns how many."""
+    rc = lib().tqr_release_plans()
+    if rc < 0:
+        raise TqrError(rc, "tqr_release_plans")
+    return rc
+
+
 def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None, wait=True):
     """End to end on host arrays: A (m x n, Fortran-ordered float64 numpy
     array) is overwritten by R and V; B (m x nrhs, Fortran order) by Q^T B.
@@ -491,6 +501,8 @@ def tqr_factor_host(A, nb, ib, tree, BS=1, B=None, stream=None, reuse=None, wait
     h = ctypes.c_void_p(reuse.ptr if reuse is not None else None)
     fn = lib().tqr_factor_host if wait else lib().tqr_factor_host_async
     rc = fn(ctypes.c_void_p(A.ctypes.data), m, n, nb, ib, int(tree), BS, bp, nrhs, _stream(stream), ctypes.byref(h))
+    if rc != 0 and h.value and (reuse is None or h.value != reuse.ptr):
+        lib().tqr_free(h)                 # a handle made by the failed call
     _check(rc, "tqr_factor_host" if wait else "tqr_factor_host_async")
     if reuse is not None and h.value == reuse.ptr:
         return reuse

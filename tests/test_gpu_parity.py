@@ -341,3 +341,65 @@ def test_host_async_on_two_streams_matches_sync():
         assert np.array_equal(v, w)
     for h in hs:
         h.free()
+
+
+def test_host_handles_of_one_shape_with_other_tiles_stay_independent():
+    """tqr_factor_host given a previous handle of the same m x n but another
+    tile size makes a new handle with a device copy of A of its own: the
+    previous handle still applies its own Q^T afterwards, a call with the
+    previous handle's parameters reuses it (bit for bit the same result), and
+    both handles free cleanly."""
+    A = np.asfortranarray(workloads.gaussian(768, 256, seed=41))
+    b = workloads.rhs(768, 1, seed=42)
+    a1 = A.copy(order="F")
+    f1 = tqr.tqr_factor_host(a1, 64, 16, tqr.GREEDY)
+    a2 = A.copy(order="F")
+    f2 = tqr.tqr_factor_host(a2, 128, 16, tqr.GREEDY, reuse=f1)
+    assert f2 is not f1 and f2.ptr != f1.ptr
+    F1 = otq.factor(A, 64, 16, tqr.GREEDY)
+    F2 = otq.factor(A, 128, 16, tqr.GREEDY)
+    compare(a1, F1.A, np.abs(F1.r()).max(), tol_for(A), "R and V, nb 64")
+    compare(a2, F2.A, np.abs(F2.r()).max(), tol_for(A), "R and V, nb 128")
+    bt = tqr.colmajor(b)
+    tqr.tqr_apply_qt(f1, bt)
+    assert tqr.tqr_sync(f1) == 0
+    compare(tqr.to_numpy(bt)[:, 0], otq.apply_qt(F1, b[:, 0]), np.linalg.norm(b), tol_for(A), "Q^T b, first handle")
+    a3 = A.copy(order="F")
+    f3 = tqr.tqr_factor_host(a3, 64, 16, tqr.GREEDY, reuse=f1)
+    assert f3 is f1
+    assert np.array_equal(a3, a1)
+    f2.free()
+    f1.free()
+
+
+def test_release_plans_keeps_live_handles_valid():
+    """tqr_release_plans drops the cached plans no handle uses; a live
+    handle still applies Q^T and refactors, and a released plan is rebuilt
+    with the same result bit for bit."""
+    A = workloads.gaussian(640, 192, seed=43)
+    b = workloads.rhs(640, 1, seed=44)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, 64, 16, tqr.BINARY)
+    assert tqr.tqr_sync(f) == 0
+    first = tqr.to_numpy(At)
+    Ag = tqr.colmajor(A)
+    g = tqr.tqr_factor(Ag, 64, 16, tqr.FIBONACCI)
+    assert tqr.tqr_sync(g) == 0
+    fib = tqr.to_numpy(Ag)
+    g.free()
+    assert tqr.tqr_release_plans() >= 1                  # at least the Fibonacci plan
+    F = otq.factor(A, 64, 16, tqr.BINARY)
+    bt = tqr.colmajor(b)
+    tqr.tqr_apply_qt(f, bt)
+    assert tqr.tqr_sync(f) == 0
+    compare(tqr.to_numpy(bt)[:, 0], otq.apply_qt(F, b[:, 0]), np.linalg.norm(b), tol_for(A), "Q^T b after release")
+    At2 = tqr.colmajor(A)
+    assert tqr.tqr_factor(At2, 64, 16, tqr.BINARY, reuse=f) is f
+    assert tqr.tqr_sync(f) == 0
+    assert np.array_equal(tqr.to_numpy(At2), first)
+    Ag2 = tqr.colmajor(A)
+    g2 = tqr.tqr_factor(Ag2, 64, 16, tqr.FIBONACCI)
+    assert tqr.tqr_sync(g2) == 0
+    assert np.array_equal(tqr.to_numpy(Ag2), fib)
+    g2.free()
+    f.free()

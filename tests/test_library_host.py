@@ -196,3 +196,29 @@ def test_factor_argument_errors_before_any_device_work():
     cp = ct.c_int64(0)
     assert L.tqr_critical_path(4096, 4096, tqr.GREEDY, 1, ct.byref(cp), None) == tqr.TQR_ERR_CAPACITY
     assert out.value is None
+
+
+def test_factor_host_argument_errors_before_any_device_work():
+    """tqr_factor_host / _async check A, m, n, nb and ib (the positions
+    tqr_factor uses) before they allocate or copy anything."""
+    L = tqr.lib()
+    ct = tqr.tqr.ctypes
+    fake = ct.c_void_p(0x1000)
+    out = ct.c_void_p(None)
+    for fn in (L.tqr_factor_host, L.tqr_factor_host_async):
+        # (A_host, m, n, nb, ib, tree, BS, B_host, nrhs, stream, out)
+        assert fn(None, 64, 32, 32, 8, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -1
+        assert fn(fake, 0, 32, 32, 8, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -2
+        assert fn(fake, -5, 32, 32, 8, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -2
+        assert fn(fake, 64, 65, 32, 8, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -3
+        assert fn(fake, 64, 32, 30, 5, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -4
+        assert fn(fake, 64, 32, 32, 12, tqr.GREEDY, 1, None, 0, None, ct.byref(out)) == -5
+        assert fn(fake, 64, 32, 32, 8, tqr.GREEDY, 1, None, 0, None, None) == -11
+        assert fn(fake, 64, 32, 32, 8, tqr.GREEDY, 1, fake, -1, None, ct.byref(out)) == -9
+    assert out.value is None
+
+
+def test_release_plans_without_cached_plans():
+    """With no plan built in this process (no GPU here), releasing drops
+    nothing and touches no device."""
+    assert tqr.tqr_release_plans() == 0
