@@ -254,7 +254,10 @@ int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, 
  * maxit steps in all.  info (host, may be NULL) receives iteration counts,
  * final backward error and phase times.  Synchronizes `stream` before
  * returning.  Allocates device workspace (m*n + n*n doubles + vectors) for the
- * call. */
+ * call.  Argument errors, checked before any device work: -k for argument k
+ * (1 A, 2 m, 3 n, 4 b, 5 x, 6 nb, 7 ib, 8 tree, 9 BS, 10 precision, 11 tol
+ * negative, NaN or infinite, 12 maxit), with nb, ib, tree and BS under
+ * tqr_factor's rules; TQR_ERR_CAPACITY as tqr_factor. */
 int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b, double* x, int nb, int ib,
               int tree, int BS, int precision, double tol, int maxit, void* stream,
               tqr_lstsq_info* info);

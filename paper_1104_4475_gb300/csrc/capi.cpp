@@ -464,18 +464,29 @@ static int check_common(double* A, int64_t m, int64_t n, int nb, int ib) {
     return TQR_OK;
 }
 
+namespace tqr {
+
+int check_factor_args(int64_t m, int64_t n, int nb, int ib, int tree, int BS) {
+    static double probe;                               // a non-null stand-in for A
+    const int rc = check_common(&probe, m, n, nb, ib);
+    if (rc != TQR_OK) return rc;
+    if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
+    const int64_t p = (m + nb - 1) / nb, q = (n + nb - 1) / nb;
+    if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
+    if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
+    return TQR_OK;
+}
+
+}  // namespace tqr
+
 extern "C" {
 
 int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, void* stream,
                tqr_factors** out) {
     try {
-        int rc = check_common(A, m, n, nb, ib);
+        if (!A) return -1;
+        const int rc = check_factor_args(m, n, nb, ib, tree, BS);
         if (rc != TQR_OK) return rc;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
-        const int p = static_cast<int>((m + nb - 1) / nb);
-        const int q = static_cast<int>((n + nb - 1) / nb);
-        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
-        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
         if (!out) return -9;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return TQR_ERR_CUDA;
@@ -490,13 +501,9 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
 int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, int precision, void* stream,
                   tqr_factors** out) {
     try {
-        int rc = check_common(A, m, n, nb, ib);
+        if (!A) return -1;
+        const int rc = check_factor_args(m, n, nb, ib, tree, BS);
         if (rc != TQR_OK) return rc;
-        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
-        const int p = static_cast<int>((m + nb - 1) / nb);
-        const int q = static_cast<int>((n + nb - 1) / nb);
-        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
-        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
         if (precision < TQR_FP64 || precision > TQR_TF32) return -8;
         if (!out) return -10;
         int dev = 0;

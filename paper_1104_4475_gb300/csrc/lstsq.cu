@@ -190,7 +190,11 @@ extern "C" int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b,
     if (n < 1 || n > m) return -3;
     if (!b) return -4;
     if (!x) return -5;
+    // m, n, nb, ib, tree, BS as tqr_factor checks them, reported at this call's positions.
+    const int fa = tqr::check_factor_args(m, n, nb, ib, tree, BS);
+    if (fa != TQR_OK) return (fa <= -4 && fa >= -7) ? fa - 2 : fa;   // nb..BS: -4..-7 -> -6..-9
     if (precision < TQR_FP64 || precision > TQR_TF32) return -10;
+    if (!(tol >= 0.0) || std::isinf(tol)) return -11;
     if (maxit < 0) return -12;
     tqr_lstsq_info local{};
     tqr_lstsq_info& I = info ? *info : local;

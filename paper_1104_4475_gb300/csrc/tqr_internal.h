@@ -40,6 +40,11 @@ struct MatDesc {
     int64_t tau_off;   // offset of this matrix's tau in tau_ge / tau_el
 };
 
+// ---- argument checks shared by the entry points (capi.cpp) ----
+// tqr_factor's m, n, nb, ib, tree and BS: TQR_OK, TQR_ERR_CAPACITY, or -k for
+// tqr_factor's invalid argument k (2 m, 3 n, 4 nb, 5 ib, 6 tree, 7 BS).
+int check_factor_args(int64_t m, int64_t n, int nb, int ib, int tree, int BS);
+
 // ---- host planner (planner.cpp) ----
 int make_elims(int p, int q, int tree, int BS, std::vector<Elim>& out);
 int validate_elims(int p, int q, const Elim* e, int64_t count);

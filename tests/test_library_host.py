@@ -222,3 +222,31 @@ def test_release_plans_without_cached_plans():
     """With no plan built in this process (no GPU here), releasing drops
     nothing and touches no device."""
     assert tqr.tqr_release_plans() == 0
+
+
+def test_lstsq_argument_errors_before_any_device_work():
+    """tqr_lstsq reports each invalid argument by its own position, before it
+    allocates anything (nb, ib, tree and BS under tqr_factor's rules)."""
+    L = tqr.lib()
+    ct = tqr.tqr.ctypes
+    fake = ct.c_void_p(0x1000)
+
+    def call(A=fake, m=64, n=32, b=fake, x=fake, nb=32, ib=8, tree=tqr.GREEDY, BS=1, prec=1, tol=1e-14, maxit=5):
+        return L.tqr_lstsq(A, m, n, b, x, nb, ib, tree, BS, prec, tol, maxit, None, None)
+
+    assert call(A=None) == -1
+    assert call(m=0) == -2
+    assert call(n=65) == -3
+    assert call(b=None) == -4
+    assert call(x=None) == -5
+    assert call(nb=30, ib=5) == -6
+    assert call(ib=12) == -7
+    assert call(tree=42) == -8
+    assert call(tree=tqr.PLASMA, BS=0) == -9
+    assert call(tree=tqr.GRASAP, BS=2) == -9                    # k > q = 1
+    assert call(prec=3) == -10
+    assert call(tol=-1.0) == -11
+    assert call(tol=float("nan")) == -11
+    assert call(tol=float("inf")) == -11
+    assert call(maxit=-1) == -12
+    assert call(m=65536, n=65536, nb=16, ib=8) == tqr.TQR_ERR_CAPACITY
