@@ -421,7 +421,12 @@ int tqr_inject_fault(int kind);
  *
  * The first call on each device looks up the device address of the scratch
  * array (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  Every call reuses the same array and
+ * before any stream capture begins.  On a stream that is being captured into
+ * a CUDA graph, the task graph is written to the device by small kernels that
+ * carry it in their parameters (a copy from the library's pageable host
+ * arrays could not be captured), so the captured work replays this call's
+ * problem whatever later calls do on the host; outside capture it is copied
+ * with cudaMemcpyAsync.  Every call reuses the same array and
  * overwrites what the previous call left in it (each launch re-initializes
  * its counters and queue); calls whose device work overlaps -- on two
  * streams without ordering between them, say -- race on the array and give

@@ -11,8 +11,10 @@
 // queue, queue head/tail -- lives in one file-scope __device__ array of fixed
 // size (kScratchBytes, 4 MiB).  Every GPU that loads the library holds that
 // array until the process exits.  The host-side graph is built in fixed
-// static arrays.  Problems whose task graph does not fit are rejected with
-// TQR_ERR_TOO_LARGE before anything is launched.
+// static arrays and uploaded into the scratch array (by cudaMemcpyAsync, or,
+// on a stream being captured into a CUDA graph, by kernels that carry the
+// words in their parameters).  Problems whose task graph does not fit are
+// rejected with TQR_ERR_TOO_LARGE before anything is launched.
 //
 // Every call shares the one array and overwrites what the previous call left
 // there (the counters and queue are re-initialized by each launch); two calls
@@ -219,6 +221,37 @@ private:
     }
 };
 
+// Upload for a stream that is being captured into a CUDA graph.  A copy from
+// pageable host memory (the static graph above) cannot be captured, so the
+// words travel as kernel parameters instead: each launch carries 1000 words
+// (4000 bytes, inside the 4 KiB parameter limit), and a captured launch keeps
+// its parameters by value, so the graph replays this call's task graph even
+// after later calls have rewritten the static arrays.
+constexpr int kPutWords = 1000;
+struct PutChunk {
+    uint32_t w[kPutWords];
+};
+
+__global__ void put_words_kernel(uint32_t* __restrict__ dst, const PutChunk c, int n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = c.w[t];
+}
+
+cudaError_t put_words(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    static_assert(sizeof(DevTask) % 4 == 0, "device tasks are whole words");
+    const uint32_t* w = static_cast<const uint32_t*>(src);
+    uint32_t* d = static_cast<uint32_t*>(dst);
+    const size_t nw = bytes / 4;
+    PutChunk c;
+    for (size_t off = 0; off < nw; off += kPutWords) {
+        const int n = static_cast<int>(std::min<size_t>(kPutWords, nw - off));
+        std::memcpy(c.w, w + off, static_cast<size_t>(n) * 4);
+        put_words_kernel<<<1, 256, 0, s>>>(d + off, c, n);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 }  // namespace tqr
 
@@ -275,14 +308,18 @@ extern "C" int tqr_factor_noalloc(double* A, int64_t m, int64_t n, int nb, int i
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nt = static_cast<size_t>(g_h.ntasks);
-    if (cudaMemcpyAsync(g.tasks, g_h.tasks, nt * sizeof(DevTask), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(g.succ_ptr, g_h.succ_ptr, (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(g.succ, g_h.succ, static_cast<size_t>(g_h.nedges) * sizeof(int32_t),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(g.indeg, g_h.indeg, nt * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(g.ready, g_h.ready, static_cast<size_t>(g_h.nready) * sizeof(int32_t),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) return TQR_ERR_CUDA;
+    if (capture == cudaStreamCaptureStatusInvalidated) return TQR_ERR_CUDA;
+    const bool capturing = capture == cudaStreamCaptureStatusActive;
+    auto upload = [&](void* dst, const void* src, size_t bytes) {
+        return capturing ? put_words(dst, src, bytes, s) : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    if (upload(g.tasks, g_h.tasks, nt * sizeof(DevTask)) != cudaSuccess ||
+        upload(g.succ_ptr, g_h.succ_ptr, (nt + 1) * sizeof(int32_t)) != cudaSuccess ||
+        upload(g.succ, g_h.succ, static_cast<size_t>(g_h.nedges) * sizeof(int32_t)) != cudaSuccess ||
+        upload(g.indeg, g_h.indeg, nt * sizeof(int32_t)) != cudaSuccess ||
+        upload(g.ready, g_h.ready, static_cast<size_t>(g_h.nready) * sizeof(int32_t)) != cudaSuccess)
         return TQR_ERR_CUDA;
 
     ExecParams P{};

@@ -107,3 +107,48 @@ def test_noalloc_rejects_ts_on_triangle_tile():
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc = tqr.tqr_factor_noalloc(A, nb, ib, elims, tau, tau.clone(), status, ts=True)
     assert rc == tqr.TQR_ERR_INVALID_LIST
+
+
+def test_noalloc_captured_in_cuda_graph_replays_tqr_factor():
+    """Captured into a CUDA graph (after a first call outside the capture, as
+    documented), each replay factors the matrix in place exactly as the
+    uncaptured call does, also after an uncaptured call for another problem
+    has rewritten the library's static graph arrays in between."""
+    m, n, nb, ib, tree = 1024, 256, 64, 16, tqr.GREEDY
+    p, q = -(-m // nb), -(-n // nb)
+    elims = tqr.tqr_elimination_list(p, q, tree)
+    A = workloads.gaussian(m, n, seed=120)
+    tau_ge = torch.zeros(p * q * nb, dtype=torch.float64, device="cuda")
+    tau_el = torch.zeros_like(tau_ge)
+    status = torch.full((1,), -999, dtype=torch.int32, device="cuda")
+    want = tqr.colmajor(A)                                  # the uncaptured call's result
+    assert tqr.tqr_factor_noalloc(want, nb, ib, elims, tau_ge, tau_el, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    want = tqr.to_numpy(want)
+    want_tau = (tau_ge.cpu().numpy(), tau_el.cpu().numpy())
+
+    At = tqr.colmajor(A)
+    pristine = At.clone()
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            rc = tqr.tqr_factor_noalloc(At, nb, ib, elims, tau_ge, tau_el, status, stream=stream)
+    assert rc == 0, tqr.tqr_strerror(rc)
+    for rep in range(2):
+        At.copy_(pristine)
+        tau_ge.zero_()
+        tau_el.zero_()
+        if rep == 1:                                        # another problem in between, uncaptured
+            B = tqr.colmajor(workloads.gaussian(300, 100, seed=121))
+            e2 = tqr.tqr_elimination_list(-(-300 // 32), -(-100 // 32), tqr.BINARY)
+            t2 = torch.zeros(10 * 4 * 32, dtype=torch.float64, device="cuda")
+            assert tqr.tqr_factor_noalloc(B, 32, 8, e2, t2, t2.clone(), status) == 0
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert np.array_equal(tqr.to_numpy(At), want)
+        assert np.array_equal(tau_ge.cpu().numpy(), want_tau[0])
+        assert np.array_equal(tau_el.cpu().numpy(), want_tau[1])
