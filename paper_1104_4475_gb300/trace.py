@@ -69,3 +69,84 @@ def edge_violations(trace, edges):
     u, v = edges[:, 0], edges[:, 1]
     bad = trace[v, 5] < trace[u, 6]
     return [tuple(e) for e in edges[bad].tolist()]
+
+
+# Weights of the six kernels in units of nb^3/3 flops (Table 1), indexed by kind.
+KERNEL_WEIGHT = (4, 6, 2, 6, 6, 12)
+
+
+def measured_critical_path(trace, edges):
+    """Longest path through the executed task graph with every task weighted
+    by its traced duration (end - start): the measured counterpart of the
+    unit-weight critical path of the Section 2.3 model.  Every edge (u, v)
+    of the executor's graphs runs from a task to a later one (task ids follow
+    program order), so one pass in id order finds it.  Returns
+    (length_ns, path), path being the task ids along it, first to last."""
+    n = len(trace)
+    if n == 0:
+        return 0, []
+    dur = (trace[:, 6] - trace[:, 5]).astype(np.int64)
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    if len(edges) and not np.all(edges[:, 0] < edges[:, 1]):
+        raise ValueError("an edge does not run from an earlier task to a later one")
+    order = np.argsort(edges[:, 1], kind="stable")
+    src, dst = edges[order, 0], edges[order, 1]
+    ptr = np.searchsorted(dst, np.arange(n + 1))
+    best = np.zeros(n, dtype=np.int64)
+    back = np.full(n, -1, dtype=np.int64)
+    for v in range(n):
+        lo, hi = ptr[v], ptr[v + 1]
+        if hi > lo:
+            preds = src[lo:hi]
+            a = int(np.argmax(best[preds]))
+            back[v] = preds[a]
+            best[v] = best[preds[a]] + dur[v]
+        else:
+            best[v] = dur[v]
+    v = int(np.argmax(best))
+    length = int(best[v])
+    path = []
+    while v >= 0:
+        path.append(v)
+        v = int(back[v])
+    return length, path[::-1]
+
+
+def task_units(trace, nb, strip, n):
+    """Work of every traced task in units of nb^3/3 flops: the kernel's
+    weight (Table 1) for a panel task, and for an update task the weight times
+    the fraction of the tile's nb columns its strip covers (strips of `strip`
+    columns; the last tile column holds n - (q-1) nb columns).  Over a whole
+    factorization with n a multiple of nb they sum to the total weight of the
+    list (6pq^2 - 2q^3 for TT kernels, Section 2.2)."""
+    q = -(-n // nb)
+    last_cols = n - (q - 1) * nb
+    units = np.empty(len(trace), dtype=np.float64)
+    for t, (kind, i, piv, k, js, s, e, sm) in enumerate(trace.tolist()):
+        w = KERNEL_WEIGHT[kind]
+        if kind in (1, 3, 5):
+            j, st = js >> 16, js & 0xffff
+            cols = last_cols if j == q - 1 else nb
+            units[t] = w * min(strip, cols - st * strip) / nb
+        else:
+            units[t] = float(w)
+    return units
+
+
+def model_prediction(trace, nb, strip, n, critical_path, n_cta, flops):
+    """The paper's performance model (Section 4) fed with measured rates:
+    gamma_seq, one CTA's rate, is the traced work over the traced busy time;
+    with T units of work, P CTAs and a unit-weight critical path cp, the model
+    predicts a makespan of max(T/P, cp) units at gamma_seq, i.e. a rate of
+    gamma_seq * T / max(T/P, cp) (flops counted per unit as nb^3/3).  Also
+    returns the makespan and rate that `flops` (the LAPACK count) gives."""
+    units = task_units(trace, nb, strip, n)
+    busy_s = float((trace[:, 6] - trace[:, 5]).sum()) / 1e9
+    unit_flops = nb ** 3 / 3.0
+    T = float(units.sum())
+    gamma_seq = T * unit_flops / busy_s if busy_s > 0 else 0.0
+    bound_units = max(T / n_cta, float(critical_path))
+    t_pred = bound_units * unit_flops / gamma_seq if gamma_seq > 0 else 0.0
+    return {"units": T, "gamma_seq_gflops": gamma_seq / 1e9, "bound": "cp" if critical_path > T / n_cta else "work",
+            "bound_units": bound_units, "gamma_pred_gflops": gamma_seq * T / bound_units / 1e9 if bound_units else 0.0,
+            "predicted_ms": 1e3 * t_pred, "predicted_lapack_gflops": flops / t_pred / 1e9 if t_pred > 0 else 0.0}
