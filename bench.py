@@ -167,17 +167,50 @@ def oracle_sample(qs=CPU_SAMPLE_QS):
     return fl, t
 
 
-def run_oracle_subprocess(steps=1):
+def run_oracle_subprocess(steps=1, threads=None, qs=CPU_SAMPLE_QS):
     """The oracle in a fresh process (spawned, before/independent of CUDA) with
-    its BLAS threads set to the host's core count.  Returns (gflops, cores)."""
-    cores = os.cpu_count() or 1
+    its BLAS threads set to `threads` (default: the host's core count), timed
+    on the sweep points qs.  Returns ([(flop, seconds)] per step, threads)."""
+    cores = threads or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = [bench.oracle_sample() for _ in range(%d)]; print(json.dumps(r))" % (ROOT, steps))
+            "r = [bench.oracle_sample(%r) for _ in range(%d)]; print(json.dumps(r))" % (ROOT, tuple(qs), steps))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1]), cores
+
+
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def single_core_oracle():
+    """The oracle on one core (one BLAS thread) on the q = 1 sweep point:
+    {"value": GFLOP/s, "sample": ...}, or None if the run fails."""
+    try:
+        res, _ = run_oracle_subprocess(1, threads=1, qs=(1,))
+    except (OSError, subprocess.SubprocessError, ValueError):
+        return None
+    return {"value": res[0][0] / res[0][1] / 1e9, "unit": "GFLOP/s", "cores": 1,
+            "sample": "one complete CPU-oracle factorization of the q = 1 point (m=%d, n=%d, nb=%d, ib=%d, Greedy)"
+                      % (M, NB, NB, IB)}
 
 
 def sample_desc():
@@ -199,7 +232,8 @@ def reference_main(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(),
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc()},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc(),
+                         "cpu_model": host_cpu_model(), "single_core": single_core_oracle()},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     emit(line)
@@ -224,7 +258,7 @@ def gpu_main(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res, cores = run_oracle_subprocess(1)        # before any CUDA call
         cpu = {"value": res[0][0] / res[0][1] / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": sample_desc()}
+               "sample": sample_desc(), "cpu_model": host_cpu_model(), "single_core": single_core_oracle()}
     build.build()
     torch.cuda.set_device(local)
     dist = None
