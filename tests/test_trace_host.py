@@ -131,3 +131,29 @@ def test_profile_case_trace_report_on_a_synthetic_trace():
     assert len(lines) == 3
     assert "(100.0 % of the makespan)" in lines[1]               # a chain: the path is everything
     assert "T = %d units" % (6 * p * q * q - 2 * q ** 3) in lines[2]
+
+
+def test_tree_report_on_a_synthetic_sweep_line():
+    """gamma_pred = gamma_seq T / max(T/P, cp) with T = 6pq^2 - 2q^3, and the
+    overheads against Greedy, on a bench line with made-up times."""
+    from paper_1104_4475_gb300 import tree_report
+    line = {"per_tree": {
+        "Greedy": {"1": {"BS": 1, "ms": 10.0, "gflops": 50.0, "critical_path_units": 16},
+                   "8": {"BS": 1, "ms": 100.0, "gflops": 800.0, "critical_path_units": 198}},
+        "BinaryTree": {"1": {"BS": 1, "ms": 20.0, "gflops": 25.0, "critical_path_units": 16},
+                       "8": {"BS": 1, "ms": 150.0, "gflops": 533.0, "critical_path_units": 338}}}}
+    rep = tree_report.sweep_report(line, m=64 * 256, nb=256, n_sm=152, peak_gflops=152 * 8.0)
+    g1 = rep["Greedy"][1]
+    assert g1["T"] == 6 * 64 - 2 and g1["bound"] == "cp"           # 382 units, cp 16 > 382 / 152
+    assert g1["gamma_pred"] == pytest.approx(8.0 * 382 / 16)
+    assert g1["frac_of_pred"] == pytest.approx(50.0 / (8.0 * 382 / 16))
+    b8 = rep["BinaryTree"][8]
+    T8 = 6 * 64 * 64 - 2 * 512
+    assert b8["T"] == T8 and b8["bound"] == "cp"
+    assert b8["gamma_pred"] == pytest.approx(8.0 * T8 / 338)
+    assert b8["cp_over_greedy"] == pytest.approx(338 / 198) and b8["time_over_greedy"] == pytest.approx(1.5)
+    wide = tree_report.sweep_report(line, m=64 * 256, nb=256, n_sm=2, peak_gflops=2 * 8.0)
+    assert wide["Greedy"][8]["bound"] == "work"                    # T / 2 > 198
+    assert wide["Greedy"][8]["gamma_pred"] == pytest.approx(8.0 * 2)
+    md = tree_report.markdown(rep)
+    assert "| Greedy |" in md and "1.00 / 1.00" in md
