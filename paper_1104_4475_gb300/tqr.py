@@ -393,6 +393,26 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _f32(t, what, numel=None, min_numel=None):
+    """Pointer of a contiguous float32 CUDA tensor, checked before the call so
+    that a wrong dtype, device, layout or size cannot reach the library."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % what)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, not %d" % (what, numel, t.numel()))
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError("%s must have at least %d elements, not %d" % (what, min_numel, t.numel()))
+    return _ptr(t)
+
+
+def _mlp_inputs(params, X):
+    if X.dim() != 2:
+        raise ValueError("X must be 2-D (samples x features)")
+    B, d = X.shape
+    return B, d, _f32(params, "params", tqr_mlp_param_count(d)), _f32(X, "X")
+
+
 def tqr_mlp_param_count(in_dim):
     n = lib().tqr_mlp_param_count(int(in_dim))
     if n < 0:
@@ -403,26 +423,28 @@ def tqr_mlp_param_count(in_dim):
 def tqr_mlp_forward(params, X, y=None, stream=None):
     """Network outputs for the rows of X (float32 CUDA tensors)."""
     import torch
-    B, d = X.shape
+    B, d, pp, px = _mlp_inputs(params, X)
     if y is None:
         y = torch.empty(B, dtype=torch.float32, device=X.device)
-    _check(lib().tqr_mlp_forward(_ptr(params), d, _ptr(X), B, _ptr(y), _stream(stream)), "tqr_mlp_forward")
+    _check(lib().tqr_mlp_forward(pp, d, px, B, _f32(y, "y", B), _stream(stream)), "tqr_mlp_forward")
     return y
 
 
 def tqr_mlp_loss_grad(params, X, t, grad, loss, work=None, stream=None):
     import torch
-    B, d = X.shape
+    B, d, pp, px = _mlp_inputs(params, X)
     if work is None:
         work = torch.empty(B * (4 * 64 + 2), dtype=torch.float32, device=X.device)
-    _check(lib().tqr_mlp_loss_grad(_ptr(params), d, _ptr(X), _ptr(t), B, _ptr(work), _ptr(grad), _ptr(loss),
+    _check(lib().tqr_mlp_loss_grad(pp, d, px, _f32(t, "t", B), B, _f32(work, "work", min_numel=B * (4 * 64 + 2)),
+                                   _f32(grad, "grad", params.numel()), _f32(loss, "loss", min_numel=1),
                                    _stream(stream)), "tqr_mlp_loss_grad")
     return work
 
 
 def tqr_mlp_adam_step(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    _check(lib().tqr_mlp_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), lr, beta1, beta2,
-                                   eps, int(step), _stream(stream)), "tqr_mlp_adam_step")
+    n = params.numel()
+    _check(lib().tqr_mlp_adam_step(_f32(params, "params"), _f32(grad, "grad", n), _f32(m, "m", n), _f32(v, "v", n),
+                                   n, lr, beta1, beta2, eps, int(step), _stream(stream)), "tqr_mlp_adam_step")
 
 
 def tqr_set_trace(f, enable=True):

@@ -250,3 +250,20 @@ def test_lstsq_argument_errors_before_any_device_work():
     assert call(tol=float("inf")) == -11
     assert call(maxit=-1) == -12
     assert call(m=65536, n=65536, nb=16, ib=8) == tqr.TQR_ERR_CAPACITY
+
+
+def test_mlp_bindings_check_tensors_before_the_call():
+    """The cost-model bindings reject anything but contiguous float32 CUDA
+    tensors of the right size before calling the library (here: CPU tensors,
+    a float64 tensor, a feature count the network does not take)."""
+    torch = pytest.importorskip("torch")
+    P = tqr.tqr_mlp_param_count(4)
+    params, X = torch.zeros(P), torch.zeros(3, 4)
+    with pytest.raises(TypeError):
+        tqr.tqr_mlp_forward(params, X)
+    with pytest.raises(TypeError):
+        tqr.tqr_mlp_loss_grad(params, X, torch.zeros(3), torch.zeros(P), torch.zeros(1))
+    with pytest.raises(TypeError):
+        tqr.tqr_mlp_adam_step(params.double(), params, params, params, 1e-3, 1)
+    with pytest.raises(tqr.TqrError):
+        tqr.tqr_mlp_forward(params, torch.zeros(3, 40))              # more than TQR_MLP_MAX_IN features
