@@ -233,7 +233,7 @@ def tqr_lstsq(A, b, x, nb, ib, tree, BS=1, precision=TQR_FP64, tol=0.0, maxit=50
     if ld != m:
         raise ValueError("A must have leading dimension m")
     info = tqr_lstsq_info()
-    rc = lib().tqr_lstsq(ptr, m, n, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nb, ib,
+    rc = lib().tqr_lstsq(ptr, m, n, _dev(b, "b", "float64", m), _dev(x, "x", "float64", n), nb, ib,
                          int(tree), BS, int(precision), float(tol), int(maxit), _stream(stream), ctypes.byref(info))
     _check(rc, "tqr_lstsq")
     return {k: getattr(info, k) for k, _ in tqr_lstsq_info._fields_}
@@ -270,9 +270,13 @@ def tqr_apply_q(f, B, stream=None):
 
 def tqr_form_t(f, T_geqrt=None, T_elim=None, stream=None):
     """Fill the T factor arrays (CUDA float64 tensors of p*q*ib*nb elements)."""
-    def p(t):
-        return ctypes.c_void_p(t.data_ptr() if t is not None else None)
-    _check(lib().tqr_form_t(ctypes.c_void_p(f.ptr), p(T_geqrt), p(T_elim), _stream(stream)), "tqr_form_t")
+    i = tqr_get_info(f)
+    elems = i["p"] * i["q"] * i["ib"] * i["nb"]
+
+    def p(t, what):
+        return ctypes.c_void_p(None) if t is None else _dev(t, what, "float64", elems)
+    _check(lib().tqr_form_t(ctypes.c_void_p(f.ptr), p(T_geqrt, "T_geqrt"), p(T_elim, "T_elim"), _stream(stream)),
+           "tqr_form_t")
 
 
 class Batch:
@@ -393,17 +397,22 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _f32(t, what, numel=None, min_numel=None):
-    """Pointer of a contiguous float32 CUDA tensor, checked before the call so
-    that a wrong dtype, device, layout or size cannot reach the library."""
+def _dev(t, what, dtype, numel=None, min_numel=None):
+    """Pointer of a contiguous CUDA tensor of `dtype`, checked before the call
+    so that a wrong dtype, device, layout or size cannot reach the library."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
-        raise TypeError("%s must be a contiguous float32 CUDA tensor" % what)
+    dtype = getattr(torch, dtype)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous %s CUDA tensor" % (what, str(dtype).replace("torch.", "")))
     if numel is not None and t.numel() != numel:
         raise ValueError("%s must have %d elements, not %d" % (what, numel, t.numel()))
     if min_numel is not None and t.numel() < min_numel:
         raise ValueError("%s must have at least %d elements, not %d" % (what, min_numel, t.numel()))
     return _ptr(t)
+
+
+def _f32(t, what, numel=None, min_numel=None):
+    return _dev(t, what, "float32", numel, min_numel)
 
 
 def _mlp_inputs(params, X):
@@ -583,10 +592,12 @@ def tqr_factor_noalloc(A, nb, ib, elims, tau_geqrt, tau_elim, status, ts=False, 
     if ld != m:
         raise ValueError("A must have leading dimension m")
     arr = np.ascontiguousarray(np.asarray(elims, dtype=np.int32).reshape(-1, 3))
+    ntau = -(-m // nb) * -(-n // nb) * nb if nb > 0 else 0
+    tg = _dev(tau_geqrt, "tau_geqrt", "float64", min_numel=ntau)
+    te = _dev(tau_elim, "tau_elim", "float64", min_numel=ntau)
+    st = _dev(status, "status", "int32", min_numel=1)
     return lib().tqr_factor_noalloc(ptr, m, n, nb, ib, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                    arr.shape[0], 1 if ts else 0, ctypes.c_void_p(tau_geqrt.data_ptr()),
-                                    ctypes.c_void_p(tau_elim.data_ptr()), ctypes.c_void_p(status.data_ptr()),
-                                    _stream(stream))
+                                    arr.shape[0], 1 if ts else 0, tg, te, st, _stream(stream))
 
 
 def tqr_set_timeout_ms(ms):

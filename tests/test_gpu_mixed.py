@@ -123,3 +123,18 @@ def test_lstsq_ill_conditioned_reports_honestly():
     assert infos["converged"] in (0, 1)
     if infos["converged"]:
         assert infos["backward_error"] <= 2 * info64["backward_error"]
+
+
+def test_lstsq_binding_rejects_wrong_vectors_before_the_call():
+    """b and x must be contiguous float64 CUDA tensors of m and n elements:
+    a short b, a float32 b and a strided x are refused before the library
+    is called."""
+    A = tqr.colmajor(workloads.gaussian(64, 32, seed=5))
+    x = torch.zeros(32, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        tqr.tqr_lstsq(A, torch.zeros(63, dtype=torch.float64, device="cuda"), x, 32, 8, tqr.GREEDY)
+    with pytest.raises(TypeError):
+        tqr.tqr_lstsq(A, torch.zeros(64, dtype=torch.float32, device="cuda"), x, 32, 8, tqr.GREEDY)
+    with pytest.raises(TypeError):
+        tqr.tqr_lstsq(A, torch.zeros(64, dtype=torch.float64, device="cuda"),
+                      torch.zeros(64, dtype=torch.float64, device="cuda")[::2], 32, 8, tqr.GREEDY)

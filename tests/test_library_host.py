@@ -267,3 +267,13 @@ def test_mlp_bindings_check_tensors_before_the_call():
         tqr.tqr_mlp_adam_step(params.double(), params, params, params, 1e-3, 1)
     with pytest.raises(tqr.TqrError):
         tqr.tqr_mlp_forward(params, torch.zeros(3, 40))              # more than TQR_MLP_MAX_IN features
+
+
+def test_vector_bindings_check_tensors_before_the_call():
+    """The device-array check that tqr_lstsq (b, x), tqr_form_t (T arrays) and
+    tqr_factor_noalloc (tau, status) apply before calling the library: on a
+    machine without a GPU it rejects every tensor, naming the argument."""
+    torch = pytest.importorskip("torch")
+    for t, dt in ((torch.zeros(64, dtype=torch.float64), "float64"), (torch.zeros(1, dtype=torch.int32), "int32")):
+        with pytest.raises(TypeError, match="status must be a contiguous %s CUDA tensor" % dt):
+            tqr.tqr._dev(t, "status", dt)
