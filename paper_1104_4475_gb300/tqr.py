@@ -254,16 +254,24 @@ def tqr_factor_list(A, nb, ib, elims, ts=False, stream=None, reuse=None):
     return Factors(h.value, A)
 
 
+def _rhs(f, B):
+    ptr, ld = _colmajor_ptr(B, "B")
+    m = tqr_get_info(f)["m"]
+    if B.shape[0] != m:
+        raise ValueError("B must have m = %d rows, not %d" % (m, B.shape[0]))
+    return ptr, ld
+
+
 def tqr_apply_qt(f, B, stream=None):
     """B <- Q^T B in place (B: column-major CUDA tensor with m rows)."""
-    ptr, ld = _colmajor_ptr(B, "B")
+    ptr, ld = _rhs(f, B)
     _check(lib().tqr_apply_qt(ctypes.c_void_p(f.ptr), ptr, ld, B.shape[1], _stream(stream)), "tqr_apply_qt")
     return B
 
 
 def tqr_apply_q(f, B, stream=None):
     """B <- Q B in place."""
-    ptr, ld = _colmajor_ptr(B, "B")
+    ptr, ld = _rhs(f, B)
     _check(lib().tqr_apply_q(ctypes.c_void_p(f.ptr), ptr, ld, B.shape[1], _stream(stream)), "tqr_apply_q")
     return B
 

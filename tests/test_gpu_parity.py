@@ -403,3 +403,15 @@ def test_release_plans_keeps_live_handles_valid():
     assert np.array_equal(tqr.to_numpy(Ag2), fib)
     g2.free()
     f.free()
+
+
+def test_apply_binding_rejects_b_with_another_row_count():
+    """B must have the factorization's m rows (a taller view with ld >= m
+    would pass the library's ldb check but apply Q to the wrong rows)."""
+    A = workloads.gaussian(256, 64, seed=45)
+    f, _ = gpu_factor(A, 64, 16, tqr.GREEDY)
+    with pytest.raises(ValueError):
+        tqr.tqr_apply_qt(f, tqr.colmajor(np.zeros((255, 1))))
+    with pytest.raises(ValueError):
+        tqr.tqr_apply_q(f, tqr.colmajor(np.zeros((300, 2)))[:255])
+    f.free()
