@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -183,14 +184,17 @@ static int get_apply_graph(Plan& P, int nstrips, bool trans, const DevGraph** ou
     return TQR_OK;
 }
 
-static double g_timeout_ms = 0.0;        // set by tqr_set_timeout_ms
-static int g_fault = 0;                  // set by tqr_inject_fault
+// Process-wide test hooks; atomic because any host thread may set them while
+// another launches.
+static std::atomic<double> g_timeout_ms{0.0};   // set by tqr_set_timeout_ms
+static std::atomic<int> g_fault{0};             // set by tqr_inject_fault
 
 static uint64_t timeout_ns(double flops) {
-    if (g_timeout_ms > 0) return static_cast<uint64_t>(g_timeout_ms * 1e6);
+    const double ms = g_timeout_ms.load();
+    if (ms > 0) return static_cast<uint64_t>(ms * 1e6);
     if (const char* s = std::getenv("TQR_TIMEOUT_MS")) {
-        const double ms = std::atof(s);
-        if (ms > 0) return static_cast<uint64_t>(ms * 1e6);
+        const double env_ms = std::atof(s);
+        if (env_ms > 0) return static_cast<uint64_t>(env_ms * 1e6);
     }
     // Longest legitimate wait is below the whole run; assume >= 50 GFLOP/s.
     return static_cast<uint64_t>((10.0 + flops / 5e10) * 1e9);
@@ -341,10 +345,7 @@ struct tqr_factors {
 // injection is pending (the counters and edges are untouched).
 static DevGraph graph_for_launch(const DevGraph& g) {
     DevGraph x = g;
-    if (g_fault == 1) {
-        x.nready = 0;
-        g_fault = 0;
-    }
+    if (g_fault.exchange(0) == 1) x.nready = 0;      // one launch consumes the injection
     return x;
 }
 
@@ -906,13 +907,13 @@ int tqr_release_plans(void) {
 }
 
 int tqr_set_timeout_ms(double ms) {
-    g_timeout_ms = ms > 0 ? ms : 0.0;
+    g_timeout_ms.store(ms > 0 ? ms : 0.0);
     return TQR_OK;
 }
 
 int tqr_inject_fault(int kind) {
     if (kind != 0 && kind != 1) return -1;
-    g_fault = kind;
+    g_fault.store(kind);
     return TQR_OK;
 }
 
