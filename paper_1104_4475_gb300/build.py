@@ -8,6 +8,7 @@ newer than the library triggers a rebuild.
 """
 
 import concurrent.futures
+import fcntl
 import os
 import shutil
 import subprocess
@@ -49,17 +50,28 @@ def needs_build():
 
 
 def build(force=False, verbose=False, extra_flags=()):
-    """Compile libtqr.so; returns its path."""
+    """Compile libtqr.so; returns its path.  Processes that build at the same
+    time take turns (a file lock in the build folder); the one that comes
+    second finds the library up to date."""
     if not force and not needs_build():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not needs_build():
+            return LIB
+        return _build(verbose, extra_flags)
+
+
+def _build(verbose, extra_flags):
+    nvcc = _nvcc()
     jobs = []
     for src in sources():
         if os.path.basename(src) == EXEC_INST:
             for g, p in EXEC_PAIRS:
                 obj = os.path.join(BUILD, "exec_g%d_p%d.o" % (g, p))
-                cmd = [nvcc, "-c", src, "-o", obj, "-DTQR_G=%d" % g, "-DTQR_PREC=%d" % p] + ARCH + FLAGS + list(extra_flags)
+                cmd = ([nvcc, "-c", src, "-o", obj, "-DTQR_G=%d" % g, "-DTQR_PREC=%d" % p] + ARCH + FLAGS
+                       + list(extra_flags))
                 jobs.append((cmd, obj))
             continue
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
