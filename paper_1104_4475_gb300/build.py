@@ -42,8 +42,27 @@ def _headers():
     return hs
 
 
+# ELF e_machine codes of the hosts the library is built on.
+_ELF_MACHINE = {"x86_64": 62, "aarch64": 183}
+
+
+def _lib_matches_host():
+    """False when LIB is an ELF file for another CPU than this one (a copy of
+    the tree moved between an x86 and an Arm machine)."""
+    import platform
+    want = _ELF_MACHINE.get(platform.machine())
+    try:
+        with open(LIB, "rb") as fh:
+            head = fh.read(20)
+    except OSError:
+        return False
+    if len(head) < 20 or head[:4] != b"\x7fELF":
+        return False
+    return want is None or int.from_bytes(head[18:20], "little") == want
+
+
 def needs_build():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not _lib_matches_host():
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in sources() + _headers() + [__file__])

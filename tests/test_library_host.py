@@ -277,3 +277,22 @@ def test_vector_bindings_check_tensors_before_the_call():
     for t, dt in ((torch.zeros(64, dtype=torch.float64), "float64"), (torch.zeros(1, dtype=torch.int32), "int32")):
         with pytest.raises(TypeError, match="status must be a contiguous %s CUDA tensor" % dt):
             tqr.tqr._dev(t, "status", dt)
+
+
+def test_build_rebuilds_a_library_for_another_cpu(tmp_path, monkeypatch):
+    """A libtqr.so for another CPU (the tree copied between an x86 and an Arm
+    machine) counts as missing, whatever its time stamp."""
+    import platform
+    from paper_1104_4475_gb300 import build as b
+    codes = b._ELF_MACHINE
+    here = codes.get(platform.machine())
+    if here is None:
+        pytest.skip("unknown host CPU")
+    other = next(c for c in codes.values() if c != here)
+    for code, ok in ((here, True), (other, False)):
+        lib = tmp_path / ("lib%d.so" % code)
+        lib.write_bytes(b"\x7fELF" + bytes(14) + code.to_bytes(2, "little") + bytes(40))
+        monkeypatch.setattr(b, "LIB", str(lib))
+        assert b._lib_matches_host() is ok
+    monkeypatch.setattr(b, "LIB", str(tmp_path / "missing.so"))
+    assert b._lib_matches_host() is False and b.needs_build()
