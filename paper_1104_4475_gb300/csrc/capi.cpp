@@ -457,7 +457,7 @@ static int check_common(double* A, int64_t m, int64_t n, int nb, int ib) {
     if (!A) return -1;
     if (m < 1) return -2;
     if (n < 1 || n > m) return -3;
-    if (nb < 4 || nb > 256 || nb % 4 != 0) return -4;
+    if (nb < 8 || nb > 256 || nb % 4 != 0) return -4;
     if (ib < 1 || ib > 64 || nb % ib != 0) return -5;
     const int64_t p = (m + nb - 1) / nb, q = (n + nb - 1) / nb;
     if (p > 65535 || q > 65535) return -2;

@@ -263,7 +263,7 @@ extern "C" int tqr_factor_noalloc(double* A, int64_t m, int64_t n, int nb, int i
     if (!A) return -1;
     if (m < 1) return -2;
     if (n < 1 || n > m) return -3;
-    if (nb < 4 || nb > 256 || nb % 4 != 0) return -4;
+    if (nb < 8 || nb > 256 || nb % 4 != 0) return -4;
     if (ib < 1 || ib > 64 || nb % ib != 0) return -5;
     if (!list && count > 0) return -6;
     if (count < 0) return -7;

@@ -182,6 +182,7 @@ def test_factor_argument_errors_before_any_device_work():
     assert L.tqr_factor(fake, 0, 32, 32, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -2
     assert L.tqr_factor(fake, 64, 65, 32, 8, tqr.GREEDY, 1, None, ct.byref(out)) == -3     # n > m
     assert L.tqr_factor(fake, 64, 32, 30, 5, tqr.GREEDY, 1, None, ct.byref(out)) == -4     # nb % 4
+    assert L.tqr_factor(fake, 64, 32, 4, 4, tqr.GREEDY, 1, None, ct.byref(out)) == -4      # nb < 8
     assert L.tqr_factor(fake, 64, 32, 32, 12, tqr.GREEDY, 1, None, ct.byref(out)) == -5    # ib does not divide nb
     assert L.tqr_factor(fake, 64, 32, 32, 8, 42, 1, None, ct.byref(out)) == -6             # unknown tree
     assert L.tqr_factor(fake, 64, 32, 32, 8, tqr.PLASMA, 0, None, ct.byref(out)) == -7     # BS < 1
