@@ -142,7 +142,7 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
  * TQR_SPLIT_TF32 / TQR_TF32 the panel kernels also form the compact-WY T of
  * each block of ib reflectors in FP64, and the update kernels apply
  * C <- C - V (T^T (V^T C)) with both products on the tensor cores; A (R and V)
- * stays FP64.  Low precision needs nb % 16 == 0 and ib in {16, 32, 64, 128}
+ * stays FP64.  Low precision needs nb % 16 == 0 and ib in {16, 32, 64}
  * (else TQR_ERR_UNSUPPORTED).  Argument errors: as tqr_factor, -8 for an
  * unknown precision, -10 for out. */
 int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, int precision,
@@ -153,8 +153,8 @@ int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int
  * The list is checked against the rules of Section 2.2 first
  * (TQR_ERR_INVALID_LIST); with ts = 1 a list that zeroes a tile already in
  * triangle form (a row that was a pivot earlier in the same column) is
- * invalid too, since TSQRT needs a square tile there.  *out is reused only if it was made from the same
- * list. */
+ * invalid too, since TSQRT needs a square tile there.  *out is reused only if
+ * it was made from the same list. */
 int tqr_factor_list(double* A, int64_t m, int64_t n, int nb, int ib, const int32_t* list,
                     int64_t count, int ts, void* stream, tqr_factors** out);
 
@@ -192,7 +192,9 @@ int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count);
 /* Dependency edges (u -> v: v may start only after u has finished) of the
  * handle's factorization graph, in the device task numbering of
  * tqr_get_trace; host only.  With a trace, every edge must satisfy
- * end(u) <= start(v) (a happens-before check of the executor).  cap in edges,
+ * end(u) <= start(v) (a happens-before check of the executor).  Every edge
+ * runs from a task to a later one (u < v: tasks are numbered in program
+ * order), so the task order is a topological order.  cap in edges,
  * *count = number of edges (TQR_ERR_CAPACITY if cap is too small). */
 int tqr_get_edges(const tqr_factors* f, int32_t* src, int32_t* dst, int64_t cap, int64_t* count);
 
@@ -302,7 +304,8 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
  * n in 65..128 needs nb = 128.  The results equal
  * tqr_factor's for the same (nb, TQR_FLAT_TS) up to rounding.  Other matrices of
  * the batch go to the task-graph executor in the same call; each kind is one
- * launch (up to three column classes + the executor), all on `stream`.
+ * launch (one per (column class 32 / 64 / 128, tile height) pair in use, up
+ * to nine, plus the executor), all on `stream`.
  *
  * tqr_factor_batched_f32: the same for FP32 matrices (all arithmetic FP32);
  * every matrix must satisfy the one-tile-column conditions above (FP32 also
