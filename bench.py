@@ -640,6 +640,9 @@ def trees_main(args):
                     best = {"BS": BS, "ms": 1e3 * t, "gflops": flops(M, NB * q) / t / 1e9,
                             "critical_path_units": cp, "cp_bound_ms": 1e3 * cp * unit_s,
                             "makespan_over_cp_bound": t / (cp * unit_s)}
+            if args.trace_cp:
+                best.update(traced_critical_path(tqr, work, src, tree, best["BS"],
+                                                 torch.cuda.get_device_properties(0).multi_processor_count))
             out.setdefault(name, {})[str(q)] = best
         del src, work
     sweep = {name: workload_flops() / sum(v[str(q)]["ms"] / 1e3 for q in QS) / 1e9 for name, v in out.items()}
@@ -653,6 +656,25 @@ def trees_main(args):
             "unit_ms": 1e3 * unit_s, "seconds": time.perf_counter() - t_all}
     emit(line)
     return 0
+
+
+def traced_critical_path(tqr, work, src, tree, BS, n_sm):
+    """One traced factorization (after an untraced one that builds the
+    handle): its traced makespan, SM busy fraction and measured critical path,
+    the longest path through the executed graph with traced task durations."""
+    from paper_1104_4475_gb300 import trace as ttrace
+    work.copy_(src)
+    h = tqr.tqr_factor(work, NB, IB, tree, BS)
+    tqr.tqr_set_trace(h, True)
+    work.copy_(src)
+    h = tqr.tqr_factor(work, NB, IB, tree, BS, reuse=h)
+    tqr.tqr_sync(h)
+    tr, edges = tqr.tqr_get_trace(h), tqr.tqr_get_edges(h)
+    h.free()
+    s = ttrace.summary(tr, n_sm)
+    cp_ns, path = ttrace.measured_critical_path(tr, edges)
+    return {"traced_makespan_ms": s["makespan_ms"], "busy_fraction": s["busy_fraction"],
+            "measured_cp_ms": cp_ns / 1e6, "measured_cp_tasks": len(path)}
 
 
 # ------------------------------------------------------- learned cost model
@@ -721,6 +743,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace-cp", action="store_true",
+                    help="--workload trees: trace one more factorization per (tree, q) at its best BS and report "
+                         "the measured critical path (longest traced path through the executed graph)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per executor launch from an ncu capture (for the roofline line)")
     args = ap.parse_args()

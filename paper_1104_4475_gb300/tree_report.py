@@ -14,7 +14,10 @@ GFLOP/s, unit-weight critical path) and prints, per (tree, q):
   strips on different SMs, which shortens the critical path below cp units, so
   the measured rate can exceed gamma_pred where the critical path binds;
 * the overhead with respect to Greedy (Greedy = 1) in critical-path length and
-  in time, as the paper's overhead figures show them.
+  in time, as the paper's overhead figures show them;
+* with `bench.py --workload trees --trace-cp`, the measured critical path (the
+  longest path through the executed graph, traced task durations) against the
+  traced makespan.
 
 For m and n multiples of nb, T * nb^3/3 equals the LAPACK count 2n^2(m - n/3),
 so gamma_pred and the measured GFLOP/s count the same flops.
@@ -47,7 +50,8 @@ def sweep_report(line, m, nb, n_sm, peak_gflops):
                        "bound": "cp" if cp > T / n_sm else "work", "gamma_pred": pred,
                        "frac_of_pred": r["gflops"] / pred,
                        "cp_over_greedy": cp / g["critical_path_units"] if g else None,
-                       "time_over_greedy": r["ms"] / g["ms"] if g else None}
+                       "time_over_greedy": r["ms"] / g["ms"] if g else None,
+                       "measured_cp_ms": r.get("measured_cp_ms"), "traced_makespan_ms": r.get("traced_makespan_ms")}
         out[tree] = dict(sorted(rows.items()))
     return out
 
@@ -67,7 +71,14 @@ def markdown(rep):
         b.append("| %s | " % tree + " | ".join(
             "%.2f / %.2f" % (rows[q]["cp_over_greedy"], rows[q]["time_over_greedy"])
             if q in rows and rows[q]["cp_over_greedy"] is not None else "" for q in qs) + " |")
-    return "\n".join(a + b)
+    c = []
+    if any(r["measured_cp_ms"] is not None for rows in rep.values() for r in rows.values()):
+        c = ["", "Measured critical path / traced makespan, ms (bench --trace-cp):", "", head, sep]
+        for tree, rows in rep.items():
+            c.append("| %s | " % tree + " | ".join(
+                "%.1f / %.1f" % (rows[q]["measured_cp_ms"], rows[q]["traced_makespan_ms"])
+                if q in rows and rows[q]["measured_cp_ms"] is not None else "" for q in qs) + " |")
+    return "\n".join(a + b + c)
 
 
 def main(argv=None):

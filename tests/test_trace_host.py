@@ -156,4 +156,7 @@ def test_tree_report_on_a_synthetic_sweep_line():
     assert wide["Greedy"][8]["bound"] == "work"                    # T / 2 > 198
     assert wide["Greedy"][8]["gamma_pred"] == pytest.approx(8.0 * 2)
     md = tree_report.markdown(rep)
-    assert "| Greedy |" in md and "1.00 / 1.00" in md
+    assert "| Greedy |" in md and "1.00 / 1.00" in md and "Measured critical path" not in md
+    line["per_tree"]["Greedy"]["8"].update(measured_cp_ms=61.5, traced_makespan_ms=99.0)
+    md = tree_report.markdown(tree_report.sweep_report(line, m=64 * 256, nb=256, n_sm=152, peak_gflops=1216.0))
+    assert "Measured critical path" in md and "61.5 / 99.0" in md
