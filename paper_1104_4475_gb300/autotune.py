@@ -25,6 +25,7 @@ TREE_CANDIDATES = [(tqr.GREEDY, 1), (tqr.BINARY, 1), (tqr.FIBONACCI, 1), (tqr.FL
 
 
 ONE_COLUMN_NB = (64, 128, 256)
+SQUARE_NB = (16, 32, 64, 128)
 
 
 def candidates(n, m_lo):
@@ -32,7 +33,7 @@ def candidates(n, m_lo):
     nb <= n with every tree, plus FlatTree-TS with one tile column (nb >= n),
     which runs each matrix in one CTA."""
     out = []
-    for nb in (16, 32, 64, 128):
+    for nb in SQUARE_NB:
         if nb > n or nb > m_lo:
             continue
         for ib in (8, 16, 32):
@@ -146,7 +147,9 @@ def load(path):
 
 def lookup(db, m, n):
     """The tuned (nb, ib, tree, BS) for an m x n matrix: its class, or the
-    nearest class in n and m."""
+    nearest class in n and m.  A square-tile choice whose nb exceeds n takes
+    the largest candidate tile size that fits n (one-column FlatTree-TS when
+    none does), so the result is always a valid configuration for (m, n)."""
     best, key = None, None
     for c in db["classes"]:
         dn = abs(np.log2(n) - np.log2(c["n"]))
@@ -154,10 +157,12 @@ def lookup(db, m, n):
         d = (dn, dm)
         if best is None or d < key:
             best, key = c, d
+    fits = [c for c in SQUARE_NB if c <= min(best["nb"], n)]
     if best["tree"] == tqr.FLAT_TS and best["nb"] >= best["n"]:     # one tile column
-        nb = max(best["nb"], -(-n // 4) * 4)
-        return min(nb, 256), 8, tqr.FLAT_TS, 1
-    nb = min(best["nb"], n)
+        return min(max(best["nb"], -(-n // 4) * 4), 256), 8, tqr.FLAT_TS, 1
+    if not fits:                                                     # n below every square tile
+        return max(ONE_COLUMN_NB[0], -(-n // 4) * 4), 8, tqr.FLAT_TS, 1
+    nb = fits[-1]
     ib = min(best["ib"], nb)
     BS = best["BS"]
     if best["tree"] == tqr.PLASMA:

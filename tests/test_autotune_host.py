@@ -36,3 +36,26 @@ def test_database_roundtrip_and_lookup(tmp_path):
     autotune.save(bad, str(p))
     with pytest.raises(ValueError):
         autotune.load(str(p))
+
+
+def _valid(cfg, m, n):
+    nb, ib, tree, BS = cfg
+    p = -(-m // nb)
+    return (8 <= nb <= 256 and nb % 4 == 0 and 1 <= ib <= 64 and nb % ib == 0
+            and (tree != tqr.PLASMA or 1 <= BS <= p))
+
+
+def test_lookup_always_returns_a_valid_configuration():
+    """Shapes outside the tuned classes (n below the class's tile size, very
+    small n, n above 256) still get a configuration the library accepts."""
+    db = {"version": autotune.DB_VERSION, "classes": [
+        {"n": 32, "m_lo": 512, "m_hi": 1024, "nb": 32, "ib": 8, "tree": tqr.GREEDY, "BS": 1},
+        {"n": 128, "m_lo": 512, "m_hi": 1024, "nb": 256, "ib": 8, "tree": tqr.FLAT_TS, "BS": 1},
+        {"n": 64, "m_lo": 512, "m_hi": 1024, "nb": 64, "ib": 32, "tree": tqr.PLASMA, "BS": 16}]}
+    assert autotune.lookup(db, 700, 30) == (16, 8, tqr.GREEDY, 1)      # nb 32 > n: largest tile <= 30
+    assert autotune.lookup(db, 700, 10) == (64, 8, tqr.FLAT_TS, 1)     # no square tile fits: one column
+    assert autotune.lookup(db, 700, 300) == (256, 8, tqr.FLAT_TS, 1)
+    for m in (40, 513, 5000, 20000):
+        for n in (1, 7, 16, 30, 33, 50, 64, 100, 128, 200, 300):
+            if n <= m:
+                assert _valid(autotune.lookup(db, m, n), m, n), (m, n)
