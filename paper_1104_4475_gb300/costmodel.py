@@ -41,6 +41,10 @@ def plasma_bs(m, nb):
 
 
 def features(m, n, nb, ib, tree, BS, prec):
+    if tree not in TREE_IDS:
+        raise ValueError("tree %d is outside the cost model's one-hot trees %s" % (tree, TREE_IDS))
+    if prec not in (0, 1, 2):
+        raise ValueError("precision %d is not 0, 1 or 2" % prec)
     p, q = -(-m // nb), -(-n // nb)
     cp = tqr.tqr_critical_path(p, q, tree, BS)
     flops = 2.0 * n * n * (m - n / 3.0)
@@ -158,6 +162,9 @@ class Model:
 
     @staticmethod
     def from_json(d):
+        if d.get("version") != 1 or d.get("features") != FEATURES:
+            raise ValueError("model file version %r with %r features; this code reads version 1 with %d"
+                             % (d.get("version"), d.get("features"), FEATURES))
         import torch
         return Model(torch.tensor(d["params"], dtype=torch.float32, device="cuda"), np.array(d["mu"], np.float32),
                      np.array(d["sd"], np.float32), float(d["ymu"]))

@@ -75,3 +75,24 @@ def test_records_roundtrip(tmp_path):
     p = tmp_path / "t.csv"
     costmodel.save_records(recs, str(p))
     assert costmodel.load_records(str(p)) == recs
+
+
+def test_features_refuse_trees_and_precisions_outside_the_model():
+    """PlasmaTree-TS (tree 9) has no one-hot slot in the trained network's
+    features; asking for it is an error, not an all-zero tree encoding."""
+    from paper_1104_4475_gb300 import costmodel, tqr
+    with pytest.raises(ValueError):
+        costmodel.features(16384, 2048, 256, 32, tqr.PLASMA_TS, 16, 0)
+    with pytest.raises(ValueError):
+        costmodel.features(16384, 2048, 256, 32, tqr.GREEDY, 1, 3)
+    assert costmodel.features(16384, 2048, 256, 32, tqr.GREEDY, 1, 0).shape == (costmodel.FEATURES,)
+
+
+def test_model_file_of_another_feature_set_is_refused():
+    from paper_1104_4475_gb300 import costmodel
+    with pytest.raises(ValueError):
+        costmodel.Model.from_json({"version": 1, "features": costmodel.FEATURES + 1, "params": [],
+                                   "mu": [], "sd": [], "ymu": 0.0})
+    with pytest.raises(ValueError):
+        costmodel.Model.from_json({"version": 2, "features": costmodel.FEATURES, "params": [],
+                                   "mu": [], "sd": [], "ymu": 0.0})
