@@ -57,7 +57,8 @@ def sweep_report(line, m, nb, n_sm, peak_gflops):
 
 
 def markdown(rep):
-    """Two markdown tables: measured / predicted rate, and overhead vs Greedy."""
+    """Markdown tables: measured / predicted rate, overhead vs Greedy, and (when
+    traced) measured critical path vs traced makespan."""
     qs = sorted({q for rows in rep.values() for q in rows})
     head = "| tree | " + " | ".join("q=%d" % q for q in qs) + " |"
     sep = "|---" * (len(qs) + 1) + "|"
