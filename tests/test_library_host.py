@@ -28,7 +28,7 @@ def built():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "tqr.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tqr_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(tqr_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol():
@@ -40,6 +40,30 @@ def test_exports_every_declared_symbol():
     out = os.popen("nm -D --defined-only %s" % tbuild.LIB).read()
     for name in names:
         assert re.search(r"\bT %s$" % name, out, flags=re.M), name
+
+
+def header_signatures():
+    """{name: number of parameters} of every function declared in tqr.h."""
+    src = open(os.path.join(ROOT, "include", "tqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(tqr_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_function_with_its_parameter_count():
+    """Each C entry point has ctypes argument types in the binding, as many
+    as the header declares parameters (a missing or extra argument would be
+    passed silently through ctypes)."""
+    sigs = header_signatures()
+    assert set(sigs) == set(header_functions())
+    L = tqr.lib()
+    for name, count in sigs.items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == count, (name, len(fn.argtypes), count)
 
 
 def test_library_is_built_for_sm103a():
