@@ -321,3 +321,28 @@ def test_build_rebuilds_a_library_for_another_cpu(tmp_path, monkeypatch):
         assert b._lib_matches_host() is ok
     monkeypatch.setattr(b, "LIB", str(tmp_path / "missing.so"))
     assert b._lib_matches_host() is False and b.needs_build()
+
+
+def test_binding_constants_equal_the_header():
+    """Tree ids, kernel kinds, precisions and status codes of the Python
+    binding are the values tqr.h defines (and the oracle's tree ids too)."""
+    import oracle
+    src = open(os.path.join(ROOT, "include", "tqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define (TQR_[A-Z_]+) \(?(-?\d+)\)?\s*$", src, flags=re.M)}
+    consts.update({k: int(v) for k, v in re.findall(r"\b(TQR_[A-Z0-9_]+) = (\d+)", src)})
+    trees = {"TQR_FLAT_TS": "FLAT_TS", "TQR_FLAT_TT": "FLAT_TT", "TQR_SAMEH_KUCK": "SAMEH_KUCK",
+             "TQR_BINARY": "BINARY", "TQR_FIBONACCI": "FIBONACCI", "TQR_GREEDY": "GREEDY", "TQR_PLASMA": "PLASMA",
+             "TQR_ASAP": "ASAP", "TQR_GRASAP": "GRASAP", "TQR_PLASMA_TS": "PLASMA_TS"}
+    for c, py in trees.items():
+        assert getattr(tqr, py) == consts[c], c
+        if hasattr(oracle, py):
+            assert getattr(oracle, py) == consts[c], c
+    for kind in ("GEQRT", "UNMQR", "TTQRT", "TTMQR", "TSQRT", "TSMQR"):
+        assert getattr(tqr.tqr, kind) == consts["TQR_" + kind], kind
+    for name in ("TQR_FP64", "TQR_SPLIT_TF32", "TQR_TF32"):
+        assert getattr(tqr, name) == consts[name], name
+    errs = [k for k in consts if k.startswith("TQR_ERR_")]
+    assert len(errs) == 9
+    for name in errs:
+        assert getattr(tqr, name) == consts[name], name
