@@ -346,3 +346,24 @@ def test_binding_constants_equal_the_header():
     assert len(errs) == 9
     for name in errs:
         assert getattr(tqr, name) == consts[name], name
+
+
+def test_binding_structs_match_the_header():
+    """tqr_info, tqr_batch_info and tqr_lstsq_info: the ctypes structures
+    have the header's fields, in its order, with its types."""
+    import ctypes
+    src = open(os.path.join(ROOT, "include", "tqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    ctype = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+    structs = re.findall(r"typedef struct \{(.*?)\}\s*(tqr_[a-z_]+);", src, flags=re.S)
+    assert {name for _, name in structs} == {"tqr_info", "tqr_batch_info", "tqr_lstsq_info"}
+    for body, name in structs:
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, names = decl.split(None, 1)
+            fields += [(nm.strip(), ctype[typ]) for nm in names.split(",")]
+        py = getattr(tqr.tqr, name)._fields_
+        assert [(f, t) for f, t in py] == fields, name
