@@ -367,3 +367,14 @@ def test_binding_structs_match_the_header():
             fields += [(nm.strip(), ctype[typ]) for nm in names.split(",")]
         py = getattr(tqr.tqr, name)._fields_
         assert [(f, t) for f, t in py] == fields, name
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without libtqr.so every entry point raises: there is no fallback."""
+    from paper_1104_4475_gb300 import build as b
+    monkeypatch.setattr(b, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(tqr.tqr, "_lib", None)
+    with pytest.raises(ImportError):
+        tqr.tqr_elimination_list(4, 2, tqr.GREEDY)
+    with pytest.raises(ImportError):
+        tqr.tqr_critical_path(4, 2, tqr.GREEDY)
