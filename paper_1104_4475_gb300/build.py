@@ -76,7 +76,10 @@ def build(force=False, verbose=False, extra_flags=()):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     with open(os.path.join(BUILD, ".lock"), "w") as lock:
-        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            fcntl.flock(lock, fcntl.LOCK_EX)
+        except OSError:
+            pass                        # a file system without locks: build unserialized
         if not force and not needs_build():
             return LIB
         return _build(verbose, extra_flags)
