@@ -11,7 +11,6 @@ replace it by ranking candidates without timing them (see ``costmodel``).
 """
 
 import json
-import os
 
 import numpy as np
 

@@ -13,7 +13,6 @@ gamma_seq * T / max(T/P, cp) with gamma_seq taken from the trace.
 """
 
 import argparse
-import os
 import sys
 
 import numpy as np
