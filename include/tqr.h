@@ -142,7 +142,7 @@ int tqr_factor(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS
  * TQR_SPLIT_TF32 / TQR_TF32 the panel kernels also form the compact-WY T of
  * each block of ib reflectors in FP64, and the update kernels apply
  * C <- C - V (T^T (V^T C)) with both products on the tensor cores; A (R and V)
- * stays FP64.  Low precision needs nb % 16 == 0 and ib in {16, 32, 64}
+ * stays FP64.  Low precision needs nb % 16 == 0, nb >= 64 and ib in {16, 32}
  * (else TQR_ERR_UNSUPPORTED).  Argument errors: as tqr_factor, -8 for an
  * unknown precision, -10 for out. */
 int tqr_factor_ex(double* A, int64_t m, int64_t n, int nb, int ib, int tree, int BS, int precision,

@@ -138,3 +138,13 @@ def test_lstsq_binding_rejects_wrong_vectors_before_the_call():
     with pytest.raises(TypeError):
         tqr.tqr_lstsq(A, torch.zeros(64, dtype=torch.float64, device="cuda"),
                       torch.zeros(64, dtype=torch.float64, device="cuda")[::2], 32, 8, tqr.GREEDY)
+
+
+def test_low_precision_refuses_layouts_not_checked_on_the_gpu():
+    """Low-precision updates run only with nb >= 64 (64-column strips) and
+    ib in {16, 32}; other configurations are refused, not run unchecked."""
+    for nb, ib in ((32, 16), (48, 16), (64, 64)):
+        A = tqr.colmajor(workloads.gaussian(256, 128, seed=6))
+        with pytest.raises(tqr.TqrError) as e:
+            tqr.tqr_factor_ex(A, nb, ib, tqr.GREEDY, 1, tqr.TQR_SPLIT_TF32)
+        assert e.value.code == tqr.TQR_ERR_UNSUPPORTED
