@@ -86,12 +86,12 @@ typedef enum {
 typedef struct {
     int32_t refine_iterations;  /* FP64 refinement steps taken                       */
     int32_t cgls_iterations;    /* R-preconditioned CGLS steps taken                  */
-    int32_t converged;          /* 1 if the backward error reached tol (always 1 in FP64) */
+    int32_t converged;          /* 1 if the backward error reached tol (FP64 with tol = 0: 1) */
     int32_t status;             /* device status of the factorization                */
     double backward_error;      /* ||A^T r||_2 / (||A||_F ||r||_2), r = b - A x      */
     double residual_norm;       /* ||r||_2                                           */
     double factor_seconds;      /* factorization + Q^T b, wall time                  */
-    double solve_seconds;       /* inverse of R, solution and refinement, wall time  */
+    double solve_seconds;       /* solution, preconditioner and refinement, wall time */
 } tqr_lstsq_info;
 
 /* Summary of a factorization handle. */
@@ -104,7 +104,8 @@ typedef struct {
     int32_t strip;         /* columns per update task on the device        */
     int64_t n_elims;       /* length of the elimination list               */
     int64_t n_tile_tasks;  /* kernel tasks (Algorithms 2/3)                */
-    int64_t n_device_tasks;/* tasks after splitting updates into strips    */
+    int64_t n_device_tasks;/* tasks after splitting updates into strips and
+                              panels into blocks (nb / ib >= 2, ib >= 8)     */
     int64_t n_edges;       /* dependency edges of the device task graph    */
     int64_t critical_path; /* unit-weight critical path, units of nb^3/3    */
     double flops;          /* 2 n^2 (m - n/3), the LAPACK count (Section 2.2) */
@@ -182,10 +183,14 @@ int tqr_form_t(tqr_factors* f, double* T_geqrt, double* T_elim, void* stream);
  * end on the GPU's %globaltimer (ns) and the SM that ran it (allocates
  * 16 bytes per task once); with TQR_TRACE set (not "0") in the environment
  * every new handle starts with tracing on.  tqr_get_trace waits for the handle's work and
- * writes 8 int64 per task to out (host): kind, i, piv, k, j * 65536 + strip,
- * start ns, end ns, SM id -- in device task order; cap in tasks, *count =
- * number of tasks (TQR_ERR_CAPACITY if cap is too small,
- * TQR_ERR_UNSUPPORTED if tracing was not enabled). */
+ * writes 8 int64 per task to out (host): kind, i, piv, k, w, start ns, end ns,
+ * SM id -- in device task order; w = j * 65536 + strip for an update strip
+ * (columns strip*W.. of tile column j, W = tqr_info.strip), -1 for a panel run
+ * as one task, and b << 32 | c_lo << 16 | c_hi for a task of block b of a panel
+ * split into blocks of ib columns: it factors the block when c_lo = b * ib,
+ * else applies the block's reflectors to columns [c_lo, c_hi) of the tile
+ * (pair).  cap in tasks, *count = number of tasks (TQR_ERR_CAPACITY if cap is
+ * too small, TQR_ERR_UNSUPPORTED if tracing was not enabled). */
 int tqr_set_trace(tqr_factors* f, int enable);
 int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count);
 
@@ -248,12 +253,14 @@ int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, 
  * use of the factorization).  A: device, m x n (m >= n), column-major, lda = m,
  * left unchanged (the library factors a copy); b: device, m; x: device, n,
  * output.  The copy of A is factored with `precision`; c = Q^T b is formed with
- * the reflectors in FP64; x = R^-1 c[0:n] with an explicit FP64 inverse of R.
- * For a low-precision factorization x is then refined in FP64 -- residual
- * r = b - A x, correction R^-1 R^-T A^T r -- until the backward error
+ * the reflectors in FP64; x solves R x = c[0:n] by blocked back substitution
+ * in FP64.  For a low-precision factorization x is then refined in FP64 --
+ * residual r = b - A x, correction R^-1 R^-T A^T r with an explicit FP64
+ * inverse of the computed R as the preconditioner -- until the backward error
  * ||A^T r|| / (||A||_F ||r||) <= tol; if a step fails to halve it, CGLS on the
  * correction problem, right-preconditioned by R^-1, continues, for at most
- * maxit steps in all.  info (host, may be NULL) receives iteration counts,
+ * maxit steps in all.  In FP64 tol is only compared with the final backward
+ * error (converged = 1 when tol = 0).  info (host, may be NULL) receives iteration counts,
  * final backward error and phase times.  Synchronizes `stream` before
  * returning.  Allocates device workspace (m*n + n*n doubles + vectors) for the
  * call.  Argument errors, checked before any device work: -k for argument k
@@ -379,6 +386,28 @@ int tqr_critical_path(int p, int q, int tree, int BS, int64_t* cp, int32_t* zero
 int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int64_t cap,
               int64_t* count);
 
+/* The device task graph that tqr_factor executes for this problem, built on
+ * the host (no GPU needed) for update strips of `strip` columns (16, 32 or 64;
+ * tqr_info.strip reports the width a GPU uses: 64 for nb >= 64 with the
+ * default shared-memory budget).  tasks (host) receives 6 ints per device
+ * task, in device order: kind, i, piv, k, j, strip.  For an update (UNMQR,
+ * TTMQR, TSMQR) j is the updated tile column and strip its column strip.  For
+ * a panel (GEQRT, TTQRT, TSQRT) run as one task j = -1; a panel split into
+ * blocks of ib columns (nb / ib >= 2 and ib >= 8) has for each block b one
+ * task j = b, strip = -1 that factors the block, then tasks j = b,
+ * strip = c_lo | c_hi << 16 that apply its reflectors to columns [c_lo, c_hi)
+ * of the same tile (pair).  src/dst (host) receive the dependency edges
+ * (src -> dst, src < dst).  Caps in tasks and edges; *ntasks and *nedges are
+ * always set (TQR_ERR_CAPACITY if a cap is too small).  Argument errors: -2 m,
+ * -3 n, -4 nb, -5 ib, -6 tree, -7 BS, -8 strip, -11 ntasks, -15 nedges NULL.
+ * The dependency rule (Section 2.3 execution model, refined to column units):
+ * a task depends on the previous writer, in program order, of every unit of
+ * gcd(ib, strip) columns it writes in each tile, and a task applying
+ * reflectors on the task that formed them. */
+int tqr_device_graph(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int strip, int32_t* tasks,
+                     int64_t task_cap, int64_t* ntasks, int32_t* src, int32_t* dst, int64_t edge_cap,
+                     int64_t* nedges);
+
 /* Test support for failure detection (the paper has no counterpart).
  * tqr_set_timeout_ms: limit, in milliseconds, for any single device wait of
  * later launches (ms <= 0 restores the default, which scales with the
@@ -411,8 +440,8 @@ int tqr_inject_fault(int kind);
  *   A:     device, m x n, column-major, lda = m; overwritten by R and V.
  *   nb, ib: as for tqr_factor.
  *   list:  host, `count` 0-based triplets (i, piv, k), e.g. from
- *          tqr_elimination_list(); checked against the Section 2.2 rules
- *          (TQR_ERR_INVALID_LIST).  ts = 1: TS kernels, 0: TT kernels;
+ *          tqr_elimination_list(); checked by the same validity rules as
+ *          tqr_factor_list (TQR_ERR_INVALID_LIST).  ts = 1: TS kernels, 0: TT kernels;
  *          with ts = 1, zeroing a tile already in triangle form is also
  *          TQR_ERR_INVALID_LIST.
  *   tau_geqrt, tau_elim: device outputs, p*q*nb doubles each; the tau of
@@ -420,7 +449,15 @@ int tqr_inject_fault(int kind);
  *          (i,k)) is stored at [((size_t)k*p + i)*nb + r].
  *   status: device output, one int32: set to 0 when the work starts and to
  *          TQR_ERR_TIMEOUT or TQR_ERR_NONFINITE if the device detects one.
- *   stream: the work is enqueued on it; the call returns without waiting.
+ *   stream: the work is enqueued on it.  Outside stream capture the task
+ *          graph is uploaded with cudaMemcpyAsync from the library's pageable
+ *          host arrays, and CUDA finishes the work already queued on `stream`
+ *          before such a copy starts: the call blocks until then.  That wait is
+ *          what lets the next call reuse the host arrays safely.  Under stream
+ *          capture nothing waits (see below).  The factorization itself is not
+ *          waited for in either case.
+ *   Device waits are bounded like tqr_factor's (tqr_set_timeout_ms,
+ *          TQR_TIMEOUT_MS), and tqr_inject_fault applies to this call too.
  *
  * The first call on each device looks up the device address of the scratch
  * array (cudaGetSymbolAddress) with that device current; make that first call

@@ -111,9 +111,12 @@ static double lapack_flops(int64_t m, int64_t n) {
 
 // Upper bound of the device tasks of a factorization graph: at most q tile
 // tasks per elimination and tile (p q of them), each update split into at
-// most nb / 8 + 1 strips.  Task ids are int32 on the device.
+// most nb / 8 + 1 strips, plus, for split panels, at most nb / 8 blocks per
+// panel (two panels per tile) with at most nb / 8 + 2 tasks each.  Task ids
+// are int32 on the device.
 static bool plan_fits(int64_t p, int64_t q, int nb) {
-    const double bound = static_cast<double>(p) * q * (q + 1) * (nb / 8 + 1);
+    const double pq = static_cast<double>(p) * q;
+    const double bound = pq * (q + 1) * (nb / 8 + 1) + 2.0 * pq * (nb / 8) * (nb / 8 + 2);
     return bound < 2.0e9;
 }
 
@@ -139,7 +142,7 @@ static int make_plan(const PlanKey& key, std::shared_ptr<Plan>& out) {
     if (!choose_layout(key.nb, key.ib, &P->G, &P->smem)) return TQR_ERR_UNSUPPORTED;
     P->W = strip_width(P->G);
     const int last_cols = static_cast<int>(key.n - static_cast<int64_t>(P->q - 1) * key.nb);
-    build_factor_graph(P->p, P->q, key.nb, P->W, last_cols, P->tt, P->g);
+    build_factor_graph(P->p, P->q, key.nb, key.ib, P->W, last_cols, P->tt, P->g);
     if (upload_graph(P->g, P->dg) != cudaSuccess) return TQR_ERR_CUDA;
     std::vector<int32_t> panels;
     for (const TileTask& x : P->tt)
@@ -189,7 +192,7 @@ static int get_apply_graph(Plan& P, int nstrips, bool trans, const DevGraph** ou
 static std::atomic<double> g_timeout_ms{0.0};   // set by tqr_set_timeout_ms
 static std::atomic<int> g_fault{0};             // set by tqr_inject_fault
 
-static uint64_t timeout_ns(double flops) {
+uint64_t exec_timeout_ns(double flops) {
     const double ms = g_timeout_ms.load();
     if (ms > 0) return static_cast<uint64_t>(ms * 1e6);
     if (const char* s = std::getenv("TQR_TIMEOUT_MS")) {
@@ -251,7 +254,7 @@ static int host_plan(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int
     std::vector<TileTask> tt;
     if (!expand_tasks(H->p, H->q, el, ts_flags(tree, BS, el), tt)) return TQR_ERR_INVALID_LIST;
     H->cp = simulate(H->p, H->q, tt, nullptr);
-    build_factor_graph(H->p, H->q, nb, W, static_cast<int>(n - static_cast<int64_t>(H->q - 1) * nb), tt, H->g);
+    build_factor_graph(H->p, H->q, nb, ib, W, static_cast<int>(n - static_cast<int64_t>(H->q - 1) * nb), tt, H->g);
     std::lock_guard<std::mutex> lk(g_hplans_mu);
     hplans()[key] = H;
     out = H;
@@ -343,11 +346,14 @@ struct tqr_factors {
 
 // A launch's graph, with the initially ready tasks dropped when a fault
 // injection is pending (the counters and edges are untouched).
-static DevGraph graph_for_launch(const DevGraph& g) {
+namespace tqr {
+DevGraph graph_for_launch(const DevGraph& g) {
     DevGraph x = g;
     if (g_fault.exchange(0) == 1) x.nready = 0;      // one launch consumes the injection
     return x;
 }
+}  // namespace tqr
+using tqr::graph_for_launch;
 
 static ExecParams base_params(const tqr_factors* f) {
     const Plan& P = *f->plan;
@@ -370,7 +376,7 @@ static ExecParams base_params(const tqr_factors* f) {
     x.V_el = f->V_el;
     x.trace = nullptr;
     x.mats = nullptr;
-    x.timeout_ns = timeout_ns(lapack_flops(P.key.m, P.key.n));
+    x.timeout_ns = exec_timeout_ns(lapack_flops(P.key.m, P.key.n));
     return x;
 }
 
@@ -563,7 +569,7 @@ static int apply_common(tqr_factors* f, double* B, int64_t ldb, int64_t nrhs, vo
         x.ldb = ldb;
         x.nrhs = nrhs;
         x.trans = trans ? 1 : 0;
-        x.timeout_ns = timeout_ns(4.0 * static_cast<double>(P.key.m) * P.key.n * nrhs);
+        x.timeout_ns = exec_timeout_ns(4.0 * static_cast<double>(P.key.m) * P.key.n * nrhs);
         cudaError_t e = launch_factor_exec(x, graph_for_launch(*g), f->ast, P.G, P.smem, false, f->stream);
         return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
     } catch (const std::bad_alloc&) {
@@ -665,7 +671,21 @@ int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count) {
             o[1] = x.i;
             o[2] = x.piv;
             o[3] = x.k;
-            o[4] = static_cast<int64_t>(x.j) * 65536 + x.strip;
+            const int kind = x.kind & 0xff;
+            if (kind == GEQRT || kind == TTQRT || kind == TSQRT) {
+                // Whole panel: -1.  Block b of a split panel: b << 32 | c_lo << 16 | c_hi,
+                // [c_lo, c_hi) the columns it factors (the block's) or updates.
+                if (x.j < 0) {
+                    o[4] = -1;
+                } else {
+                    const int64_t j0 = static_cast<int64_t>(x.j) * P.key.ib;
+                    const int64_t lo = x.strip < 0 ? j0 : (x.strip & 0xffff);
+                    const int64_t hi = x.strip < 0 ? j0 + P.key.ib : (x.strip >> 16);
+                    o[4] = (static_cast<int64_t>(x.j) << 32) | (lo << 16) | hi;
+                }
+            } else {
+                o[4] = static_cast<int64_t>(x.j) * 65536 + x.strip;
+            }
             o[5] = static_cast<int64_t>(raw[2 * t]);
             o[6] = static_cast<int64_t>(raw[2 * t] + (raw[2 * t + 1] & 0x00ffffffffffffffull));
             o[7] = static_cast<int64_t>(raw[2 * t + 1] >> 56);
@@ -883,6 +903,54 @@ int tqr_tasks(int p, int q, int tree, int BS, int32_t* out, int64_t* finish, int
     }
 }
 
+int tqr_device_graph(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int strip, int32_t* tasks,
+                     int64_t task_cap, int64_t* ntasks, int32_t* src, int32_t* dst, int64_t edge_cap,
+                     int64_t* nedges) {
+    try {
+        static double probe;
+        const int rc = check_common(&probe, m, n, nb, ib);
+        if (rc != TQR_OK) return rc == -1 ? TQR_ERR_INTERNAL : rc;   // -2 m, -3 n, -4 nb, -5 ib
+        if (tree < TQR_FLAT_TS || tree > TQR_PLASMA_TS) return -6;
+        const int p = static_cast<int>((m + nb - 1) / nb), q = static_cast<int>((n + nb - 1) / nb);
+        if ((tree == TQR_PLASMA || tree == TQR_PLASMA_TS) && (BS < 1 || BS > p)) return -7;
+        if (tree == TQR_GRASAP && (BS < 0 || BS > q)) return -7;
+        if (strip != 16 && strip != 32 && strip != 64) return -8;
+        if (!ntasks || !nedges) return !ntasks ? -11 : -15;
+        if (!plan_fits(p, q, nb)) return TQR_ERR_CAPACITY;
+        const int t = tree == TQR_SAMEH_KUCK ? TQR_FLAT_TT : tree;
+        std::vector<Elim> el;
+        int r2 = make_elims(p, q, t, BS, el);
+        if (r2 != TQR_OK) return r2;
+        std::vector<TileTask> tt;
+        if (!expand_tasks(p, q, el, ts_flags(t, BS, el), tt)) return TQR_ERR_INTERNAL;
+        Graph g;
+        build_factor_graph(p, q, nb, ib, strip, static_cast<int>(n - static_cast<int64_t>(q - 1) * nb), tt, g);
+        *ntasks = static_cast<int64_t>(g.tasks.size());
+        *nedges = static_cast<int64_t>(g.succ.size());
+        if (*ntasks > task_cap || *nedges > edge_cap) return TQR_ERR_CAPACITY;
+        if ((!tasks && *ntasks) || ((!src || !dst) && *nedges)) return TQR_ERR_CAPACITY;
+        for (size_t x = 0; x < g.tasks.size(); ++x) {
+            const DevTask& d = g.tasks[x];
+            int32_t* o = tasks + 6 * x;
+            o[0] = d.kind & 0xff;
+            o[1] = d.i;
+            o[2] = d.piv;
+            o[3] = d.k;
+            o[4] = d.j;
+            o[5] = d.strip;
+        }
+        int64_t e = 0;
+        for (size_t u = 0; u + 1 < g.succ_ptr.size(); ++u)
+            for (int32_t k = g.succ_ptr[u]; k < g.succ_ptr[u + 1]; ++k, ++e) {
+                src[e] = static_cast<int32_t>(u);
+                dst[e] = g.succ[k];
+            }
+        return TQR_OK;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
+}
+
 int tqr_release_plans(void) {
     try {
         int dropped = 0;
@@ -928,7 +996,7 @@ static int launch_batch(tqr_batch* b) {
     P.tau_el = b->tau_el;
     P.trans = 1;
     P.mats = b->d_mats;
-    P.timeout_ns = timeout_ns(b->flops);
+    P.timeout_ns = exec_timeout_ns(b->flops);
     P.nb = b->nb.empty() ? 0 : b->nb[0];
     P.ib = b->ib.empty() ? 0 : b->ib[0];
     const cudaError_t e = launch_factor_exec(P, b->dg.d, b->st, b->G, b->smem, false, b->stream);

@@ -324,78 +324,146 @@ template <int MODE>
 __device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch);
 template <int G, int MODE, int PREC>
 __device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
-                                  int ncol, double* smem);
+                                  int c_lo, int c_hi, double* smem);
 
 // ----------------------------------------------------------------------------
 // Panel kernels: GEQRT(i,k) (MODE GE), TTQRT(i,piv,k) (TT), TSQRT(i,piv,k)
 // (TS).  Blocks of ib columns are factored in turn; after each block its
 // reflectors are applied to the rest of the tile (pair), W columns at a time.
+// The executor runs a panel either as one task (panel_task) or as separate
+// tasks per block -- panel_factor(b), then panel_update(b, columns) for the
+// columns right of the block -- so that other CTAs apply block b while the
+// next block is factored; the arithmetic on every element is the same.
 // ----------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void stage_panel_block(const Smem& S, const View& top, const View& bot, int nb, int j0,
+                                                  int ib) {
+    if (MODE == GE) {
+        load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
+    } else {
+        load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib);
+        load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
+    }
+}
+
+// Factor block j0 of the panel: stage it, factor it, store R, V and tau (and,
+// in low precision, the block's FP32 V and T).  A block right of the tile's
+// last valid column only records identity reflectors (tau = 0, T = 0).
 template <int G, int MODE, int PREC>
-__device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* smem) {
-    constexpr int W = kThreads / G;
+__device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0, double* smem) {
     const Smem S = layout<G>(P, smem);
     const int nb = P.nb, ib = P.ib;
     const View bot = tile_view(P, i, k);                    // GE: the tile itself
     const View top = (MODE == GE) ? bot : tile_view(P, piv, k);
     double* tau_out = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
-    const int ncol = bot.cv;                                // valid columns of the tile pair
-    for (int j0 = 0; j0 < nb; j0 += ib) {
-        // Stage the panel block.
-        __syncthreads();
-        if (MODE == GE) {
-            load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
-        } else {
-            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib);
-            load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
-        }
-        __syncthreads();
-        factor_block<MODE>(S, nb, j0, ib, P.status);
-        // Write the block back: R (and V) in place, tau to the handle.
-        if (MODE == GE) {
-            store_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib, false);
-        } else {
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib, true);
-            store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
-        }
-        for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
+    const int64_t tile = static_cast<int64_t>(k) * P.p + i;
+    if (j0 >= bot.cv) {
+        for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = 0.0;
         if (PREC != 0) {
-            // T_b in FP64 (Cs is free here), then the trailing columns of the
-            // tile pair on the tensor cores.
-            const int64_t tile = static_cast<int64_t>(k) * P.p + i;
-            float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
-            float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
-            for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
-                const int r = idx % nb, jj = idx / nb, j = j0 + jj;
-                float v;
-                if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * nb]));
-                else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * nb]) : 0.0f;
-                else v = static_cast<float>(S.Vs[r + jj * nb]);
-                Vdst[r + static_cast<int64_t>(j) * nb] = v;
-            }
-            form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
-            panel_lp_trailing<G, MODE, PREC>(P, i, k, top, bot, j0, ncol, smem);
-        } else {
-            // Trailing update of the columns right of the block.
-            for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
-                __syncthreads();
-                if (MODE == GE) {
-                    load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W);
-                } else {
-                    load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-                    load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W);
-                }
-                __syncthreads();
-                apply_block<G, MODE>(S, nb, j0, ib, 1, ncol - c0);
-                __syncthreads();
-                if (MODE == GE) {
-                    store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, W, false);
-                } else {
-                    store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
-                    store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, W, false);
-                }
-            }
+            float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb + static_cast<int64_t>(j0) * ib;
+            float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb + static_cast<int64_t>(j0) * nb;
+            for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) Tdst[idx] = 0.0f;
+            for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) Vdst[idx] = 0.0f;
         }
+        return;
+    }
+    __syncthreads();
+    stage_panel_block<MODE>(S, top, bot, nb, j0, ib);
+    __syncthreads();
+    factor_block<MODE>(S, nb, j0, ib, P.status);
+    // Write the block back: R (and V) in place, tau to the handle.
+    if (MODE == GE) {
+        store_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib, false);
+    } else {
+        store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib, true);
+        store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
+    }
+    for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
+    if (PREC != 0) {
+        // T_b in FP64 (Cs is free here), V_b and T_b stored as FP32.
+        float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
+        float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
+        for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
+            const int r = idx % nb, jj = idx / nb, j = j0 + jj;
+            float v;
+            if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * nb]));
+            else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * nb]) : 0.0f;
+            else v = static_cast<float>(S.Vs[r + jj * nb]);
+            Vdst[r + static_cast<int64_t>(j) * nb] = v;
+        }
+        form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
+    }
+}
+
+// Apply the reflectors of block j0 (factored and stored by panel_factor) to
+// columns [c_lo, c_hi) of the tile (pair).  staged: the block's V and tau are
+// still in shared memory from panel_factor in this CTA; otherwise they are
+// loaded from the tile and the handle.  Only columns [c_lo, c_hi) are stored.
+template <int G, int MODE, int PREC>
+__device__ void panel_update(const ExecParams& P, int i, int piv, int k, int j0, int c_lo, int c_hi, bool staged,
+                             double* smem) {
+    constexpr int W = kThreads / G;
+    const int nb = P.nb, ib = P.ib;
+    const View bot = tile_view(P, i, k);
+    const View top = (MODE == GE) ? bot : tile_view(P, piv, k);
+    if (c_hi > bot.cv) c_hi = bot.cv;
+    if (c_lo >= c_hi) return;
+    if (PREC != 0) {
+        panel_lp_trailing<G, MODE, PREC>(P, i, k, top, bot, j0, c_lo, c_hi, smem);
+        return;
+    }
+    const Smem S = layout<G>(P, smem);
+    if (!staged) {
+        const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
+        __syncthreads();
+        if (MODE == GE) load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
+        else load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
+        for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
+    }
+    for (int c0 = c_lo; c0 < c_hi; c0 += W) {
+        const int nc = (c_hi - c0 < W) ? c_hi - c0 : W;
+        __syncthreads();
+        if (MODE == GE) {
+            load_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, nc);
+        } else {
+            load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, nc);
+            load_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, nc);
+        }
+        __syncthreads();
+        apply_block<G, MODE>(S, nb, j0, ib, 1, nc);
+        __syncthreads();
+        if (MODE == GE) {
+            store_rect(S.Cs, S.ldc, 0, bot, j0, nb, c0, nc, false);
+        } else {
+            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, nc, false);
+            store_rect(S.Cs, S.ldc, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, c0, nc, false);
+        }
+    }
+}
+
+// The whole panel as one task: every block factored, then applied to the
+// columns right of it.
+template <int G, int MODE, int PREC>
+__device__ void panel_task(const ExecParams& P, int i, int piv, int k, double* smem) {
+    const int nb = P.nb, ib = P.ib;
+    const int ncol = tile_view(P, i, k).cv;                 // valid columns of the tile pair
+    for (int j0 = 0; j0 < nb; j0 += ib) {
+        panel_factor<G, MODE, PREC>(P, i, piv, k, j0, smem);
+        if (j0 < ncol) panel_update<G, MODE, PREC>(P, i, piv, k, j0, j0 + ib, ncol, true, smem);
+    }
+}
+
+// A panel task of the device graph.  T.j < 0: the whole panel; otherwise one
+// block b = T.j: T.strip < 0 factors it, else T.strip = c_lo | c_hi << 16
+// applies it to columns [c_lo, c_hi).
+template <int G, int MODE, int PREC>
+__device__ __forceinline__ void panel_any(const ExecParams& P, const DevTask& T, double* smem) {
+    if (T.j < 0) {
+        panel_task<G, MODE, PREC>(P, T.i, T.piv, T.k, smem);
+    } else if (T.strip < 0) {
+        panel_factor<G, MODE, PREC>(P, T.i, T.piv, T.k, T.j * P.ib, smem);
+    } else {
+        panel_update<G, MODE, PREC>(P, T.i, T.piv, T.k, T.j * P.ib, T.strip & 0xffff, T.strip >> 16, false, smem);
     }
 }
 
@@ -733,13 +801,13 @@ __device__ void update_task_lp(const ExecParams& P, const DevTask& T, double* sm
     if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, 0, nb, c0, W);
 }
 
-// Trailing update of a panel task in low precision: block j0's FP32 V and T
-// (just written to the handle) come back by cp.async; the trailing columns
-// [j0+ib, ncol) of the tile pair are converted to FP32 strip by strip and
+// Trailing update of a panel block in low precision: block j0's FP32 V and T
+// (written to the handle by panel_factor) come by cp.async; the columns
+// [c_lo, c_hi) of the tile pair are converted to FP32 strip by strip and
 // updated on the tensor cores.  The whole shared memory is free here.
 template <int G, int MODE, int PREC>
 __device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
-                                  int ncol, double* smem) {
+                                  int c_lo, int c_hi, double* smem) {
     constexpr int W = kThreads / G;
     const int nb = P.nb, ib = P.ib;
     const Lp2 L = lp2_layout<G>(nb, ib, smem);
@@ -758,15 +826,16 @@ __device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View&
         cp_async16(L.Tb[0] + 4 * idx, Tt + static_cast<int64_t>(j0) * ib + 4 * idx);
     cp_commit();
     cp_wait<0>();
-    for (int c0 = j0 + ib; c0 < ncol; c0 += W) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += W) {
+        const int nc = (c_hi - c0 < W) ? c_hi - c0 : W;
         __syncthreads();
-        strip_to_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
-        if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
+        strip_to_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, nc);
+        if (MODE != GE) strip_to_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, nc);
         __syncthreads();
         lp2_block<G, MODE, PREC>(L, L.Vb[0], L.Tb[0], ib, j0, rlo, rhi);
         __syncthreads();
-        strip_from_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, W);
-        if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, W);
+        strip_from_f32(L.Cf, L.ldc, bot, rlo, rhi, c0, nc);
+        if (MODE != GE) strip_from_f32(L.Ctf, L.ldc, top, j0, j0 + ib, c0, nc);
     }
 }
 
@@ -779,9 +848,9 @@ __device__ __forceinline__ void update_any(const ExecParams& P, const DevTask& T
 template <int G, int PREC>
 __device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
     switch (T.kind & 0xff) {
-        case GEQRT: panel_task<G, GE, PREC>(P, T.i, -1, T.k, smem); break;
-        case TTQRT: panel_task<G, TT, PREC>(P, T.i, T.piv, T.k, smem); break;
-        case TSQRT: panel_task<G, TS, PREC>(P, T.i, T.piv, T.k, smem); break;
+        case GEQRT: panel_any<G, GE, PREC>(P, T, smem); break;
+        case TTQRT: panel_any<G, TT, PREC>(P, T, smem); break;
+        case TSQRT: panel_any<G, TS, PREC>(P, T, smem); break;
         case UNMQR: update_any<G, GE, PREC>(P, T, smem); break;
         case TTMQR: update_any<G, TT, PREC>(P, T, smem); break;
         case TSMQR: update_any<G, TS, PREC>(P, T, smem); break;

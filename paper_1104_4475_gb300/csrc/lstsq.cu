@@ -3,9 +3,11 @@
 // FP64:
 //   1. factor a copy of A (FP64, or FP64 panels + split-TF32 / TF32 updates);
 //   2. c = Q^T b with the stored reflectors applied in FP64;
-//   3. Rinv = R^-1 (explicit FP64 inverse of the computed R, one warp per
-//      column), x = Rinv c[0:n];
-//   4. low precision: corrected semi-normal-equation refinement in FP64,
+//   3. x = R^-1 c[0:n] by blocked back substitution on the computed R (FP64,
+//      backward stable);
+//   4. low precision: Rinv = R^-1, an explicit FP64 inverse of the computed R
+//      (one warp per column), serves as the preconditioner of a corrected
+//      semi-normal-equation refinement in FP64,
 //        r = b - A x,  s = A^T r,  x += Rinv Rinv^T s,
 //      until the backward error ||A^T r|| / (||A||_F ||r||) reaches tol; if it
 //      stops decreasing, R-preconditioned CGLS (min ||A Rinv z - b||, x =
@@ -92,6 +94,47 @@ __global__ void tri_inverse_kernel(const double* __restrict__ R, int64_t lda, in
     }
 }
 
+// One step of the blocked back substitution that solves R x = y for upper-
+// triangular R = triu(R[0:n, 0:n]) (lda), block rows of kBk from the bottom:
+// step kb solves the diagonal block R[r0:r1, r0:r1] x[r0:r1] = y[r0:r1] and
+// subtracts R[0:r0, r0:r1] x[r0:r1] from y[0:r0].  Every CTA solves the small
+// triangle itself (one warp, column-oriented, in shared memory) and then
+// updates its own rows of y; CTA 0 writes x[r0:r1].  Rows r0.. of y are only
+// read during the step, rows < r0 only written by the CTA that owns them.
+constexpr int kBk = 64;
+__global__ void trsv_step_kernel(const double* __restrict__ R, int64_t lda, int64_t n, int64_t r0,
+                                 double* __restrict__ y, double* __restrict__ x) {
+    __shared__ double Rd[kBk][kBk + 1];
+    __shared__ double xs[kBk];
+    const int64_t r1 = std::min<int64_t>(n, r0 + kBk);
+    const int nbk = static_cast<int>(r1 - r0);
+    for (int t = threadIdx.x; t < kBk * kBk; t += blockDim.x) {
+        const int r = t % kBk, c = t / kBk;
+        Rd[r][c] = (r < nbk && c < nbk && r <= c) ? R[(r0 + r) + (r0 + c) * lda] : 0.0;
+    }
+    for (int t = threadIdx.x; t < kBk; t += blockDim.x) xs[t] = t < nbk ? y[r0 + t] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int j = nbk - 1; j >= 0; --j) {
+            const double xj = xs[j] / Rd[j][j];
+            __syncwarp();
+            if (lane == 0) xs[j] = xj;
+            for (int i = lane; i < j; i += 32) xs[i] = fma(-Rd[i][j], xj, xs[i]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t < nbk; t += blockDim.x) x[r0 + t] = xs[t];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < r0;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nbk; ++c) acc = fma(R[i + (r0 + c) * lda], xs[c], acc);
+        y[i] -= acc;
+    }
+}
+
 // y = G v (trans = 0) or G^T v (trans = 1) for upper-triangular G (n x n, ldg).
 __global__ void trmv_kernel(const double* __restrict__ G, int64_t ldg, int64_t n, const double* __restrict__ v,
                             double* __restrict__ y, int trans) {
@@ -170,6 +213,13 @@ struct Solver {
     }
     void resid() { resid_kernel<<<grid_rows(), kT, 0, st>>>(A, m, m, n, x, b, w.r); }   // r = b - A x
     void atr(const double* r, double* s) { atr_kernel<<<grid_cols(n), kT, 0, st>>>(A, m, m, n, r, s); }
+    // x = R^-1 y for R = triu(Af[0:n, 0:n]); y (n entries) is overwritten.
+    void back_substitute(double* y, double* xo) {
+        for (int64_t r0 = ((n - 1) / kBk) * kBk; r0 >= 0; r0 -= kBk) {
+            const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, (r0 + kT - 1) / kT)));
+            trsv_step_kernel<<<g, kT, 0, st>>>(w.Af, m, n, r0, y, xo);
+        }
+    }
     void gmul(const double* v, double* y, int trans) {
         trmv_kernel<<<grid_cols(n), kT, 0, st>>>(w.Gi, n, n, v, y, trans);
     }
@@ -229,8 +279,9 @@ extern "C" int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b,
     }
     I.factor_seconds = seconds_since(t0);
     auto t1 = std::chrono::steady_clock::now();
-    tri_inverse_kernel<<<S.grid_cols(n), kT, 0, S.st>>>(S.w.Af, m, n, S.w.Gi, n);
-    S.gmul(S.w.c, x, 0);                                   // x = Rinv c[0:n]
+    S.back_substitute(S.w.c, x);                           // x = R^-1 c[0:n] (c[0:n] overwritten)
+    if (precision != TQR_FP64)                             // preconditioner of the refinement
+        tri_inverse_kernel<<<S.grid_cols(n), kT, 0, S.st>>>(S.w.Af, m, n, S.w.Gi, n);
     const double normA = std::sqrt(S.dot(A, A, static_cast<int64_t>(mn)));
     auto backward = [&](double* rnorm) {                   // r, s = A^T r, eta
         S.resid();
@@ -292,7 +343,7 @@ extern "C" int tqr_lstsq(const double* A, int64_t m, int64_t n, const double* b,
     I.solve_seconds = seconds_since(t1);
     I.backward_error = eta;
     I.residual_norm = rnorm;
-    I.converged = (precision == TQR_FP64 || eta <= tol) ? 1 : 0;
+    I.converged = ((precision == TQR_FP64 && tol == 0.0) || eta <= tol) ? 1 : 0;
     I.status = tqr_sync(f);
     tqr_free(f);
     if (e != cudaSuccess) return TQR_ERR_CUDA;

@@ -334,12 +334,7 @@ extern "C" int tqr_factor_noalloc(double* A, int64_t m, int64_t n, int nb, int i
     P.tau_ge = tau_geqrt;
     P.tau_el = tau_elim;
     P.trans = 1;
-    double limit_s = 10.0 + 2.0 * static_cast<double>(n) * n * (m - n / 3.0) / 5e10;
-    if (const char* e = std::getenv("TQR_TIMEOUT_MS")) {
-        const double ms = std::atof(e);
-        if (ms > 0) limit_s = ms / 1e3;
-    }
-    P.timeout_ns = static_cast<uint64_t>(limit_s * 1e9);
+    P.timeout_ns = exec_timeout_ns(2.0 * static_cast<double>(n) * n * (m - n / 3.0));
     // The launch resets the counters, queue, head/tail and *status first.
-    return launch_factor_exec(P, g, st, G, smem, true, s) == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+    return launch_factor_exec(P, graph_for_launch(g), st, G, smem, true, s) == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }

@@ -395,57 +395,100 @@ static void finish_graph(const std::vector<std::pair<int32_t, int32_t>>& edges, 
         if (g.indeg[t] == 0) g.ready.push_back(static_cast<int32_t>(t));
 }
 
-// Updates are split into strips of W columns; each strip of a tile has its
-// own chain of writers, while a panel kernel writes all strips of its tiles.
-void build_factor_graph(int p, int q, int nb, int W, int n_cols_last,
+bool split_panels(int nb, int ib) { return ib >= 8 && nb / ib >= 2; }
+
+// Updates are split into strips of W columns.  Panels are one task each, or,
+// when split_panels(nb, ib), one task per block b of ib columns that factors
+// it, then tasks that apply it to the columns right of it: first the next
+// look-ahead columns (max(ib, 32) of them, which the next block's factor
+// waits for), then the rest in strips of W.  Writers of a tile are chained per
+// unit of gcd(ib, W) columns, in list order: a task depends on the last
+// writer of every unit it writes, and an update also on the panel task that
+// produced its reflectors (the factor of the panel's last block, which
+// follows every other task of the panel).
+void build_factor_graph(int p, int q, int nb, int ib, int W, int n_cols_last,
                         const std::vector<TileTask>& tt, Graph& g) {
-    const int smax = (nb + W - 1) / W;
-    auto nstrips = [&](int j) {
-        const int cols = (j == q - 1) ? n_cols_last : nb;
-        return (cols + W - 1) / W;
-    };
+    const bool split = split_panels(nb, ib);
+    int cu = W;                                       // column unit of the writer chains
+    if (split) {
+        int a = ib, b = W;
+        while (b) { const int r = a % b; a = b; b = r; }
+        cu = a;
+    }
+    const int umax = (nb + cu - 1) / cu;
+    auto cols_of = [&](int j) { return (j == q - 1) ? n_cols_last : nb; };
     const size_t ntile = static_cast<size_t>(p) * q;
-    std::vector<int32_t> last(ntile * smax, -1), prod(ntile * 2, -1);
-    auto L = [&](int r, int c, int s) -> int32_t& {
-        return last[(static_cast<size_t>(c) * p + r) * smax + s];
+    std::vector<int32_t> last(ntile * umax, -1), prod(ntile * 2, -1);
+    auto L = [&](int r, int c, int u) -> int32_t& {
+        return last[(static_cast<size_t>(c) * p + r) * umax + u];
     };
     g.tasks.clear();
     std::vector<std::pair<int32_t, int32_t>> edges;
     edges.reserve(tt.size() * 4);
-    int32_t deps[2 * 64 + 2];
-    auto add_edges = [&](int32_t t, int nd) {
-        std::sort(deps, deps + nd);
-        for (int a = 0; a < nd; ++a)
+    std::vector<int32_t> deps;
+    deps.reserve(2 * umax + 4);
+    auto add_edges = [&](int32_t t) {
+        std::sort(deps.begin(), deps.end());
+        for (size_t a = 0; a < deps.size(); ++a)
             if (deps[a] >= 0 && (a == 0 || deps[a] != deps[a - 1])) edges.push_back({deps[a], t});
+        deps.clear();
     };
+    // Task t writes columns [c0, c1) of tile column c in tile rows r0 (and r1 >= 0).
+    auto writes = [&](int32_t t, int r0, int r1, int c, int c0, int c1) {
+        const int u0 = c0 / cu, u1 = (c1 + cu - 1) / cu;
+        for (int u = u0; u < u1; ++u) {
+            deps.push_back(L(r0, c, u));
+            L(r0, c, u) = t;
+            if (r1 >= 0) {
+                deps.push_back(L(r1, c, u));
+                L(r1, c, u) = t;
+            }
+        }
+    };
+    auto push = [&](int32_t kind, int i, int piv, int k, int j, int strip) {
+        const int32_t t = static_cast<int32_t>(g.tasks.size());
+        g.tasks.push_back({kind, i, piv, k, j, strip});
+        return t;
+    };
+    const int la = ((ib > 32 ? ib : 32) + ib - 1) / ib * ib;   // look-ahead columns
     for (const TileTask& x : tt) {
         if (x.kind == GEQRT || x.kind == TTQRT || x.kind == TSQRT) {
-            const int32_t t = static_cast<int32_t>(g.tasks.size());
-            g.tasks.push_back({x.kind, x.i, x.piv, x.k, -1, 0});
-            int nd = 0;
-            const int rows[2] = {x.i, x.piv};
-            const int nr = (x.kind == GEQRT) ? 1 : 2;
-            for (int a = 0; a < nr; ++a)
-                for (int s = 0; s < nstrips(x.k); ++s) {
-                    deps[nd++] = L(rows[a], x.k, s);
-                    L(rows[a], x.k, s) = t;
+            const int r1 = (x.kind == GEQRT) ? -1 : x.piv;
+            const int ncol = cols_of(x.k);
+            int32_t sink;
+            if (!split) {
+                sink = push(x.kind, x.i, x.piv, x.k, -1, 0);
+                writes(sink, x.i, r1, x.k, 0, ncol);
+                add_edges(sink);
+            } else {
+                int32_t prev = -1;
+                for (int b = 0; b < nb / ib; ++b) {
+                    const int j0 = b * ib;
+                    const int32_t f = push(x.kind, x.i, x.piv, x.k, b, -1);
+                    deps.push_back(prev);
+                    if (j0 < ncol) writes(f, x.i, r1, x.k, j0, std::min(j0 + ib, ncol));
+                    add_edges(f);
+                    prev = f;
+                    for (int c0 = j0 + ib; c0 < ncol;) {
+                        const int c1 = std::min(ncol, c0 == j0 + ib ? c0 + la : c0 + W);
+                        const int32_t u = push(x.kind, x.i, x.piv, x.k, b, c0 | (c1 << 16));
+                        deps.push_back(f);
+                        writes(u, x.i, r1, x.k, c0, c1);
+                        add_edges(u);
+                        c0 = c1;
+                    }
                 }
-            add_edges(t, nd);
-            prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == GEQRT ? 0 : 1)] = t;
+                sink = prev;
+            }
+            prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == GEQRT ? 0 : 1)] = sink;
         } else {
             const int32_t pr = prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == UNMQR ? 0 : 1)];
-            for (int s = 0; s < nstrips(x.j); ++s) {
-                const int32_t t = static_cast<int32_t>(g.tasks.size());
-                g.tasks.push_back({x.kind, x.i, x.piv, x.k, x.j, s});
-                int nd = 0;
-                deps[nd++] = pr;
-                deps[nd++] = L(x.i, x.j, s);
-                L(x.i, x.j, s) = t;
-                if (x.kind != UNMQR) {
-                    deps[nd++] = L(x.piv, x.j, s);
-                    L(x.piv, x.j, s) = t;
-                }
-                add_edges(t, nd);
+            const int ncol = cols_of(x.j);
+            for (int s = 0; s * W < ncol; ++s) {
+                const int32_t t = push(x.kind, x.i, x.piv, x.k, x.j, s);
+                deps.push_back(pr);
+                writes(t, x.i, x.kind == UNMQR ? -1 : x.piv, x.j, s * W, std::min(ncol, (s + 1) * W));
+                add_edges(t);
             }
         }
     }

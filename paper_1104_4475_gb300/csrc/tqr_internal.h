@@ -28,8 +28,9 @@ struct DevTask {
     int32_t i;       // row of the tile factored / zeroed / updated
     int32_t piv;     // pivot row (TT/TS kernels), else -1
     int32_t k;       // panel column
-    int32_t j;       // update column (updates), else -1
-    int32_t strip;   // column strip (updates), else 0
+    int32_t j;       // update column (updates); panels: -1, or the block of a split panel
+    int32_t strip;   // column strip (updates); split panel: -1 = factor the block,
+                     // else c_lo | c_hi << 16 = apply it to columns [c_lo, c_hi)
 };
 
 // One matrix of a batched factorization (device array indexed by DevTask::kind >> 8).
@@ -64,9 +65,13 @@ struct Graph {
     std::vector<int32_t> ready;      // tasks with in-degree 0, program order
 };
 
-// Graph of the factorization: updates split into strips of W columns.
+// Graph of the factorization: updates split into strips of W columns, and
+// panels, when split_panels(nb, ib), into one factor task per block of ib
+// columns plus tasks applying each block to column ranges right of it
+// (DevTask: j = block, strip = -1 to factor, else c_lo | c_hi << 16).
 // n_cols_last: number of valid columns of the last tile column.
-void build_factor_graph(int p, int q, int nb, int W, int n_cols_last,
+bool split_panels(int nb, int ib);
+void build_factor_graph(int p, int q, int nb, int ib, int W, int n_cols_last,
                         const std::vector<TileTask>& tt, Graph& g);
 // Graph replaying the panel tasks' transformations on a right-hand side of
 // nstrips strips (trans = Q^T order, else reverse order for Q).
@@ -138,6 +143,14 @@ template <int G, int PREC>
 cudaError_t launch_exec(const ExecParams& P, int smem, int grid, cudaStream_t s);
 cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState& st, int G,
                                int smem, bool reset_status, cudaStream_t s);
+// Limit for any single device wait of a launch doing `flops` flops: the value
+// of tqr_set_timeout_ms if set, else TQR_TIMEOUT_MS from the environment, else
+// 10 s + flops / 5e10 s (capi.cpp).
+uint64_t exec_timeout_ns(double flops);
+// The graph a launch should use: `g` itself, or `g` with no initially ready
+// task when tqr_inject_fault(1) is pending (one launch consumes it), so that
+// every wait of that launch runs out (capi.cpp).
+DevGraph graph_for_launch(const DevGraph& g);
 // Batched FlatTree-TS for one tile column (q = 1): one CTA per matrix, the tile
 // in registers, R in shared memory.  A matrix of n <= 128 columns with n <= nb
 // and nb in {64, 128, 256} (nb >= its column class 32 / 64 / 128; FP64 with

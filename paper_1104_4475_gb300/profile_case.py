@@ -70,7 +70,7 @@ def trace_report(tr, edges, info, n_sm):
     s = ttrace.summary(tr, n_sm)
     cp_ns, path = ttrace.measured_critical_path(tr, edges)
     model = ttrace.model_prediction(tr, info["nb"], info["strip"], info["n"], info["critical_path"], n_sm,
-                                    info["flops"])
+                                    info["flops"], info.get("ib"))
     return ["trace: makespan %.3f ms, SMs busy %.1f %%, busy ms per kind %s"
             % (s["makespan_ms"], 100 * s["busy_fraction"], {k: round(v, 3) for k, v in s["busy_ms_per_kind"].items()}),
             "trace: measured critical path %.3f ms over %d tasks (%.1f %% of the makespan)"

@@ -94,6 +94,7 @@ def lib():
             "tqr_validate_list": [i32, i32, pi32, i64],
             "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
             "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
+            "tqr_device_graph": [i64, i64, i32, i32, i32, i32, i32, pi32, i64, pi64, pi32, pi32, i64, pi64],
             "tqr_set_trace": [vp, i32],
             "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
                                    ctypes.POINTER(vp)],
@@ -588,6 +589,25 @@ def tqr_tasks(p, q, tree, BS=1):
                            fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), out.shape[0], ctypes.byref(cnt)),
            "tqr_tasks")
     return out[: cnt.value], fin[: cnt.value]
+
+
+def tqr_device_graph(m, n, nb, ib, tree, BS=1, strip=64):
+    """The device task graph of tqr_factor for this problem, built on the
+    host: (tasks (ntasks, 6) int32: kind, i, piv, k, j, strip; edges
+    (nedges, 2) int32: src, dst)."""
+    nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().tqr_device_graph(m, n, nb, ib, int(tree), BS, strip, None, 0, ctypes.byref(nt), None, None, 0,
+                                ctypes.byref(ne))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_device_graph")
+    tasks = np.zeros((max(1, nt.value), 6), dtype=np.int32)
+    src = np.zeros(max(1, ne.value), dtype=np.int32)
+    dst = np.zeros(max(1, ne.value), dtype=np.int32)
+    p32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().tqr_device_graph(m, n, nb, ib, int(tree), BS, strip, tasks.ctypes.data_as(p32), tasks.shape[0],
+                                  ctypes.byref(nt), src.ctypes.data_as(p32), dst.ctypes.data_as(p32), src.shape[0],
+                                  ctypes.byref(ne)), "tqr_device_graph")
+    return tasks[: nt.value], np.stack([src[: ne.value], dst[: ne.value]], axis=1)
 
 
 def tqr_factor_noalloc(A, nb, ib, elims, tau_geqrt, tau_elim, status, ts=False, stream=None):

@@ -1,8 +1,11 @@
 """Per-task device traces of the executor (tqr_set_trace / tqr_get_trace):
 Chrome-trace export and summaries.
 
-A trace row is (kind, i, piv, k, j * 65536 + strip, start ns, end ns, SM),
-0-based tile indices, one row per device task.
+A trace row is (kind, i, piv, k, w, start ns, end ns, SM), 0-based tile
+indices, one row per device task.  For an update strip w = j * 65536 + strip;
+for a panel run as one task w = -1; for a task of block b of a panel split
+into blocks, w = b << 32 | c_lo << 16 | c_hi: it factors the block's own
+columns (c_lo = b * ib) or applies the block to columns [c_lo, c_hi).
 """
 
 import json
@@ -12,13 +15,31 @@ import numpy as np
 KIND_NAMES = ("GEQRT", "UNMQR", "TTQRT", "TTMQR", "TSQRT", "TSMQR")
 
 
+PANEL_KINDS = (0, 2, 4)
+
+
+def panel_part(w):
+    """(block, c_lo, c_hi) of a panel task's trace word, or None for a panel
+    run as one task."""
+    if w < 0:
+        return None
+    return w >> 32, (w >> 16) & 0xffff, w & 0xffff
+
+
+def task_label(kind, i, piv, k, w):
+    if kind in PANEL_KINDS:
+        part = panel_part(w)
+        extra = "" if part is None else " b%d [%d,%d)" % part
+        return "%s(%d,%d,%d)%s" % (KIND_NAMES[kind], i, piv, k, extra)
+    return "%s(%d,%d,%d,%d/%d)" % (KIND_NAMES[kind], i, piv, k, w >> 16, w & 0xffff)
+
+
 def to_chrome(trace, path=None):
     """Chrome trace-event JSON (one track per SM); written to path if given."""
     t0 = int(trace[:, 5].min()) if len(trace) else 0
     ev = []
     for kind, i, piv, k, js, s, e, sm in trace.tolist():
-        j, strip = (js >> 16, js & 0xffff) if js >= 0 else (-1, 0)
-        name = "%s(%d,%d,%d%s)" % (KIND_NAMES[kind], i, piv, k, "" if j < 0 else ",%d/%d" % (j, strip))
+        name = task_label(kind, i, piv, k, js)
         ev.append({"name": name, "cat": KIND_NAMES[kind], "ph": "X", "pid": 0, "tid": int(sm),
                    "ts": (s - t0) / 1e3, "dur": max(0, e - s) / 1e3})
     doc = {"traceEvents": ev, "displayTimeUnit": "ns"}
@@ -49,8 +70,9 @@ def producer_violations(trace):
     every producer edge."""
     end = {}
     for kind, i, piv, k, js, s, e, sm in trace.tolist():
-        if kind in (0, 2, 4):
-            end[(kind, i, piv if kind else -1, k)] = e
+        if kind in PANEL_KINDS:                 # a split panel ends with its last task
+            key = (kind, i, piv if kind else -1, k)
+            end[key] = max(end.get(key, e), e)
     bad = []
     for kind, i, piv, k, js, s, e, sm in trace.tolist():
         if kind in (1, 3, 5):
@@ -112,35 +134,67 @@ def measured_critical_path(trace, edges):
     return length, path[::-1]
 
 
-def task_units(trace, nb, strip, n):
+def panel_part_flops(kind, nb, ib, b, c_lo, c_hi, ncol):
+    """Flops of one task of a split panel (block b, columns [c_lo, c_hi)):
+    applying reflector j to one column costs 4 (t_j + 1) flops with t_j the
+    length of its tail (nb - j - 1 for GEQRT, j + 1 for TTQRT, nb for TSQRT);
+    forming it, about 3 t_j.  The factor task forms the block's reflectors and
+    applies each to the block's later columns; an update task applies the
+    block to its columns."""
+    def tail(j):
+        return nb - j - 1 if kind == 0 else (j + 1 if kind == 2 else nb)
+    j0 = b * ib
+    if c_lo == j0:                               # the factor task
+        if j0 >= ncol:
+            return 0.0
+        return float(sum(3 * tail(j) + 4 * (tail(j) + 1) * (j0 + ib - 1 - j) for j in range(j0, j0 + ib)))
+    return float(sum(4 * (tail(j) + 1) * (c_hi - c_lo) for j in range(j0, j0 + ib)))
+
+
+def task_units(trace, nb, strip, n, ib=None):
     """Work of every traced task in units of nb^3/3 flops: the kernel's
-    weight (Table 1) for a panel task, and for an update task the weight times
-    the fraction of the tile's nb columns its strip covers (strips of `strip`
-    columns; the last tile column holds n - (q-1) nb columns).  Over a whole
-    factorization with n a multiple of nb they sum to the total weight of the
-    list (6pq^2 - 2q^3 for TT kernels, Section 2.2)."""
+    weight (Table 1) for a panel run as one task; for a task of a split panel
+    (needs ib) the weight times its share of the panel's flops
+    (panel_part_flops over the panel's tasks); for an update task the weight
+    times the fraction of the tile's nb columns its strip covers (strips of
+    `strip` columns; the last tile column holds n - (q-1) nb columns).  Over a
+    whole factorization with n a multiple of nb they sum to the total weight
+    of the list (6pq^2 - 2q^3 for TT kernels, Section 2.2)."""
     q = -(-n // nb)
     last_cols = n - (q - 1) * nb
     units = np.empty(len(trace), dtype=np.float64)
+    parts = {}                                   # panel -> [(task, flops)]
     for t, (kind, i, piv, k, js, s, e, sm) in enumerate(trace.tolist()):
         w = KERNEL_WEIGHT[kind]
-        if kind in (1, 3, 5):
+        if kind in PANEL_KINDS:
+            part = panel_part(js)
+            if part is None:
+                units[t] = float(w)
+            else:
+                if ib is None:
+                    raise ValueError("a split panel's work needs ib")
+                ncol = last_cols if k == q - 1 else nb
+                parts.setdefault((kind, i, piv, k), []).append(
+                    (t, panel_part_flops(kind, nb, ib, part[0], part[1], part[2], ncol)))
+        else:
             j, st = js >> 16, js & 0xffff
             cols = last_cols if j == q - 1 else nb
             units[t] = w * min(strip, cols - st * strip) / nb
-        else:
-            units[t] = float(w)
+    for (kind, i, piv, k), lst in parts.items():
+        tot = sum(f for _, f in lst)
+        for t, f in lst:
+            units[t] = KERNEL_WEIGHT[kind] * (f / tot if tot > 0 else 1.0 / len(lst))
     return units
 
 
-def model_prediction(trace, nb, strip, n, critical_path, n_cta, flops):
+def model_prediction(trace, nb, strip, n, critical_path, n_cta, flops, ib=None):
     """The paper's performance model (Section 4) fed with measured rates:
     gamma_seq, one CTA's rate, is the traced work over the traced busy time;
     with T units of work, P CTAs and a unit-weight critical path cp, the model
     predicts a makespan of max(T/P, cp) units at gamma_seq, i.e. a rate of
     gamma_seq * T / max(T/P, cp) (flops counted per unit as nb^3/3).  Also
     returns the makespan and rate that `flops` (the LAPACK count) gives."""
-    units = task_units(trace, nb, strip, n)
+    units = task_units(trace, nb, strip, n, ib)
     busy_s = float((trace[:, 6] - trace[:, 5]).sum()) / 1e9
     unit_flops = nb ** 3 / 3.0
     T = float(units.sum())

@@ -109,6 +109,31 @@ def test_lstsq_reaches_fp64_backward_error(kappa):
         assert np.linalg.norm(xt_ - xnp) / np.linalg.norm(xnp) <= kappa * 1e-13
 
 
+def backward_error(A, b, x):
+    r = b - A @ x
+    return np.linalg.norm(A.T @ r) / (np.linalg.norm(A) * np.linalg.norm(r))
+
+
+@pytest.mark.parametrize("n,nb", [(300, 64), (512, 128)])
+def test_lstsq_fp64_backward_error_matches_lapack(n, nb):
+    """The FP64 path solves R x = Q^T b by back substitution, so its backward
+    error stays within a small factor of LAPACK's (numpy lstsq) at kappa = 1e6,
+    also when n is not a multiple of the substitution's 64-row blocks."""
+    m, ib, kappa = 4096, 16, 1e6
+    A, b, _ = workloads.ls_problem(m, n, kappa, seed=7)
+    x64, info64, _ = solve(A, b, nb, ib, tqr.TQR_FP64)
+    xnp = np.linalg.lstsq(A, b, rcond=None)[0]
+    eta_np = backward_error(A, b, xnp)
+    eta_gpu = backward_error(A, b, x64)
+    assert info64["converged"] == 1 and info64["status"] == 0
+    assert abs(info64["backward_error"] - eta_gpu) <= 0.1 * eta_gpu      # the reported eta is this eta
+    assert eta_gpu <= 4 * eta_np, (eta_gpu, eta_np)
+    assert np.linalg.norm(x64 - xnp) / np.linalg.norm(xnp) <= kappa * 1e-13
+    # With a target, FP64 reports whether its backward error met it.
+    _, info_t, _ = solve(A, b, nb, ib, tqr.TQR_FP64, tol=eta_gpu / 1e3)
+    assert info_t["converged"] == 0
+
+
 def test_lstsq_ill_conditioned_reports_honestly():
     """kappa = 1e10 with split-TF32: kappa * u_s >> 1, plain refinement cannot
     contract; the solver hands over to preconditioned CGLS and reports whether

@@ -254,7 +254,19 @@ def test_timeout_is_reported_and_context_survives():
         f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
         assert tqr.tqr_sync(f, raise_on_error=False) == tqr.TQR_ERR_TIMEOUT
         f.free()
+        # The allocation-free entry point honours the same limit and injection.
+        nb, ib = 64, 16
+        p, q = -(-A.shape[0] // nb), -(-A.shape[1] // nb)
+        tau = torch.zeros(p * q * nb, dtype=torch.float64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        tqr.tqr_inject_fault(1)
+        rc = tqr.tqr_factor_noalloc(tqr.colmajor(A), nb, ib, tqr.tqr_elimination_list(p, q, tqr.GREEDY), tau,
+                                    tau.clone(), status)
+        assert rc == 0, tqr.tqr_strerror(rc)
+        torch.cuda.synchronize()
+        assert int(status.item()) == tqr.TQR_ERR_TIMEOUT
     finally:
+        tqr.tqr_inject_fault(0)
         tqr.tqr_set_timeout_ms(0)
     At = tqr.colmajor(A)
     f = tqr.tqr_factor(At, 64, 16, tqr.GREEDY)
