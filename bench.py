@@ -44,7 +44,10 @@ SEED = 1
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # FP32 (FFMA) peak from unit counts: 152 SMs x 128 FMA/clk/SM (256 flop) x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12
-CPU_SAMPLE_QS = (1, 2)
+# Sweep points the CPU oracle is timed on: in the GPU arm's cpu_baseline (one
+# pass, about 25 s on 16 Arm cores) and, per step, in the reference arm.
+CPU_SAMPLE_QS = (1, 2, 4)
+REF_SAMPLE_QS = (1, 2)
 # DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the q = 8 launch of this sweep
 # (5.602 GB for 1.3174e11 flop).  The traffic comes from re-staging reflector
@@ -56,6 +59,34 @@ TRAFFIC_BYTES_PER_FLOP = 5.602e9 / 1.3174e11
 
 def flops(m, n):
     return 2.0 * n * n * (m - n / 3.0)
+
+
+PEAK_KINDS = (("dfma_tflops", 0), ("dmma_tflops", 1), ("ffma_tflops", 2), ("tf32_mma_tflops", 3))
+
+
+def measure_peaks(tqr, torch, seconds=0.2):
+    """Peak rates of this GPU (TFLOP/s) from the library's probes
+    (tqr_peak_probe): FP64 FMA, FP64 mma.sync, FP32 FMA and TF32 mma.sync,
+    each one launch of about `seconds` timed with CUDA events after a
+    calibration launch."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kind in PEAK_KINDS:
+        iters = 2000
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = tqr.tqr_peak_probe(kind, iters, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            rate = fl / t
+            iters = max(1000, int(iters * seconds / max(t, 1e-6)))
+        out[name] = rate / 1e12
+    out["how"] = ("tqr_peak_probe: 2 CTAs x 8 warps per SM, independent chains of one instruction "
+                  "(8 FMA chains per thread; 4 mma accumulators per warp), one launch of ~%.1f s each, CUDA events"
+                  % seconds)
+    return out
 
 
 def workload_flops(qs=QS):
@@ -213,16 +244,24 @@ def single_core_oracle():
                       % (M, NB, NB, IB)}
 
 
-def sample_desc():
-    return ("complete CPU-oracle factorizations of the q in %s points of the sweep (m=%d, nb=%d, ib=%d, Greedy), "
-            "%.3g flop" % (list(CPU_SAMPLE_QS), M, NB, IB, workload_flops(CPU_SAMPLE_QS)))
+def sample_desc(qs=CPU_SAMPLE_QS):
+    return ("complete CPU-oracle factorizations of the q in %s points of the sweep (m=%d, nb=%d, ib=%d, Greedy, "
+            "the bench's tree for these q), %.3g flop = %.2f %% of the sweep's flops"
+            % (list(qs), M, NB, IB, workload_flops(qs), 100.0 * workload_flops(qs) / workload_flops()))
+
+
+def cpu_estimate(rate_gflops):
+    """The whole sweep on the CPU oracle at the sampled rate (a stated
+    estimate: the oracle's rate depends little on q, all BLAS-2 work)."""
+    return {"sweep_seconds_estimate": workload_flops() / (rate_gflops * 1e9),
+            "basis": "sweep flops / the sampled rate (not measured: the full sweep would take hours on the oracle)"}
 
 
 def reference_main(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    res, cores = run_oracle_subprocess(args.warmup + args.steps)
+    res, cores = run_oracle_subprocess(args.warmup + args.steps, qs=REF_SAMPLE_QS)
     timed = res[args.warmup:]
     fl = sum(r[0] for r in timed)
     t = sum(r[1] for r in timed)
@@ -232,7 +271,8 @@ def reference_main(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(),
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc(),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample_desc(REF_SAMPLE_QS) + ", per step",
                          "cpu_model": host_cpu_model(), "single_core": single_core_oracle()},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -257,10 +297,14 @@ def gpu_main(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res, cores = run_oracle_subprocess(1)        # before any CUDA call
-        cpu = {"value": res[0][0] / res[0][1] / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": sample_desc(), "cpu_model": host_cpu_model(), "single_core": single_core_oracle()}
+        rate = res[0][0] / res[0][1] / 1e9
+        cpu = {"value": rate, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_desc(),
+               "seconds": res[0][1], "cpu_model": host_cpu_model(), "single_core": single_core_oracle()}
+        cpu.update(cpu_estimate(rate))
     build.build()
     torch.cuda.set_device(local)
+    peaks = measure_peaks(tqr, torch)
+    fp64_peak = peaks["dfma_tflops"]
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -393,28 +437,79 @@ def gpu_main(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak,
                          "traffic": args.traffic if args.traffic is not None
                          else TRAFFIC_BYTES_PER_FLOP * workload_flops(),
                          "traffic_unit": "bytes per step (7 launches), estimated from the DRAM bytes per "
                                          "flop of an ncu capture of the Greedy q = 8 launch",
                          "algorithmic_bytes": sum(16.0 * M * NB * q for q in QS),
                          "kernel": "exec_kernel<4> (persistent executor; events around each tqr_factor)",
-                         "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)"},
+                         "peak_source": "measured in this run: FP64 FMA probe (DFMA; the executor's "
+                                        "arithmetic), of measured",
+                         "peak_unit_count": FP64_PEAK_TFLOPS,
+                         "frac_of_unit_count": achieved / FP64_PEAK_TFLOPS},
+            "measured_peaks": peaks,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": timed_launches,
-            "fp64_pct_of_peak": 100.0 * value / 1e3 / FP64_PEAK_TFLOPS / world,
+            "fp64_pct_of_peak": 100.0 * value / 1e3 / fp64_peak / world,
             "detail": detail,
         }
-        emit(line)
     for h in handles.values():
         h.free()
+    handles.clear()
+    del pristine, work, flush
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if world == 1 and not args.no_next_rows:
+            line["next_rows"] = next_rows(args)
+        emit(line)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def next_rows(args):
+    """The rest of the headline metric, measured after the sweep (outside its
+    timed region): the mixed-precision least-squares speedup at the FP64
+    path's backward error, the batched tall-skinny rates and the learned cost
+    model's pick, each from its own workload (--workload lstsq / batched /
+    costmodel) run with one timed step.  A row that fails records its error."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup = 1, 3
+    out = {}
+    try:
+        ls = lstsq_line(a)
+        out["lstsq"] = {"metric": ls["metric"], "value": ls["value"], "unit": "x", "config": ls["config"]["workload"],
+                        "per_kappa": {k: {x: v[x] for x in ("speedup", "fp64_seconds", "mixed_seconds",
+                                                             "fp64_backward_error", "mixed_backward_error",
+                                                             "converged", "refine_iterations", "cgls_iterations",
+                                                             "forward_error_mixed_vs_fp64")}
+                                      for k, v in ls["detail"].items()}}
+    except Exception as e:                       # noqa: BLE001 - reported, not hidden
+        out["lstsq"] = {"error": repr(e)}
+    try:
+        bt = batched_line(a)
+        d = bt["detail"]
+        out["batched"] = {"metric": bt["metric"], "value": bt["value"], "unit": "GFLOP/s",
+                          "fp64_kernel_gflops": d["tuned"]["kernel_gflops"], "fp64_frac": bt["roofline"]["frac"],
+                          "fp32_gflops": d["fp32_tuned"]["gflops"], "fp32_kernel_gflops": d["fp32_tuned"]["kernel_gflops"],
+                          "fp32_frac": bt["roofline"]["fp32_frac"],
+                          "fixed_config_gflops": d["fixed_nb64_ib16_greedy"]["gflops"],
+                          "speedup_tuned_vs_fixed": d["speedup_tuned_vs_fixed"],
+                          "peaks_of_measured": {"fp64": bt["roofline"]["peak"], "fp32": bt["roofline"]["fp32_peak"]}}
+    except Exception as e:                       # noqa: BLE001
+        out["batched"] = {"error": repr(e)}
+    try:
+        cm = costmodel_line(a)
+        out["costmodel"] = {"metric": cm["metric"], "value": cm["value"], "unit": "x", "data": cm["data"],
+                            "fp64": cm["detail"]["fp64"], "split_tf32": cm["detail"]["split_tf32"]}
+    except Exception as e:                       # noqa: BLE001
+        out["costmodel"] = {"error": repr(e)}
+    return out
 
 
 # ----------------------------------------------------- mixed-precision LS
@@ -428,6 +523,11 @@ LS_KAPPAS = (1e2, 1e6, 1e10)
 
 
 def lstsq_main(args):
+    emit(lstsq_line(args))
+    return 0
+
+
+def lstsq_line(args):
     """Mixed-precision least squares (split-TF32 updates, FP64 panels, FP64
     refinement) against the FP64 path on A = U diag(sigma) V^T, 65536 x 4096,
     kappa in {1e2, 1e6, 1e10}, b = A x_true + 1e-10 N(0,1).  Times are wall
@@ -482,8 +582,7 @@ def lstsq_main(args):
                                    "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
                        "nb": LS_NB, "ib": LS_IB, "tree": "%s(BS=%d)" % (LS_TREE, LS_BS), "kappas": list(LS_KAPPAS)},
             "detail": detail}
-    emit(line)
-    return 0
+    return line
 
 
 # --------------------------------------------------- batched tall-skinny QR
@@ -491,6 +590,30 @@ BT_COUNT, BT_SEED = 4096, 3
 
 
 def batched_main(args):
+    emit(batched_line(args))
+    return 0
+
+
+DATA_DIR = os.path.join(ROOT, "paper_1104_4475_gb300", "data")
+TUNE_DB = os.path.join(DATA_DIR, "autotune_batched_gb300.json")
+TUNE_DB32 = os.path.join(DATA_DIR, "autotune_batched_f32_gb300.json")
+
+
+def load_or_tune(autotune, path, sample, f32=False):
+    """The tuner database at `path` if it exists, else a fresh tuning run
+    (written to `path` when one is given).  Returns (db, tuning seconds or
+    None when loaded)."""
+    if path and os.path.exists(path):
+        return autotune.load(path), None
+    t = time.perf_counter()
+    db = autotune.tune(sample=sample, f32=f32)
+    t = time.perf_counter() - t
+    if path:
+        autotune.save(db, path)
+    return db, t
+
+
+def batched_line(args):
     """4096 independent FP64 matrices, m ~ U[512, 16384], n in {32, 64, 128},
     N(0,1) entries, factored in one persistent launch captured in a CUDA
     graph, with (nb, ib, tree) per size class from the autotuner.  A step
@@ -501,17 +624,11 @@ def batched_main(args):
     from paper_1104_4475_gb300 import autotune, build
     build.build()
     torch.cuda.set_device(0)
+    peaks = measure_peaks(tqr, torch)
     rng = np.random.default_rng(BT_SEED)
     ms = rng.integers(512, 16385, BT_COUNT)
     ns = rng.choice([32, 64, 128], BT_COUNT)
-    t_tune = time.perf_counter()
-    if args.tune_db and os.path.exists(args.tune_db):
-        db = autotune.load(args.tune_db)
-    else:
-        db = autotune.tune(sample=args.tune_sample)
-        if args.tune_db:
-            autotune.save(db, args.tune_db)
-    t_tune = time.perf_counter() - t_tune
+    db, t_tune = load_or_tune(autotune, args.tune_db, args.tune_sample)
     g = torch.Generator(device="cuda").manual_seed(BT_SEED)
     src = [torch.randn(int(n), int(m), generator=g, dtype=torch.float64, device="cuda").t() for m, n in zip(ms, ns)]
     work = [torch.empty_like(s.t()).t() for s in src]
@@ -563,9 +680,7 @@ def batched_main(args):
     fixed_cfgs = [(min(64, int(n)), 16, tqr.GREEDY, 1) for n in ns]
     fixed = measure(fixed_cfgs)
     # FP32: the same shapes, FlatTree-TS with one tile column, tile height tuned per class.
-    t32 = time.perf_counter()
-    db32 = autotune.tune(sample=args.tune_sample, f32=True)
-    t32 = time.perf_counter() - t32
+    db32, t32 = load_or_tune(autotune, args.tune_db32, args.tune_sample, f32=True)
     src = [s.float() for s in src]
     src = [s.t().contiguous().t() for s in src]
     work = [torch.empty_like(s.t()).t() for s in src]
@@ -578,37 +693,46 @@ def batched_main(args):
             "config": {"workload": "4096 FP64 matrices, m ~ U[512,16384], n in {32,64,128}, N(0,1); one "
                                    "persistent launch replayed from a CUDA graph; step = input restore + replay",
                        "count": BT_COUNT, "flops_per_step": flops},
-            "roofline": {"bound": "alu", "achieved": tuned["kernel_gflops"] / 1e3, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": tuned["kernel_gflops"] / 1e3 / FP64_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": tuned["kernel_gflops"] / 1e3, "peak": peaks["dfma_tflops"],
+                         "unit": "TFLOP/s", "frac": tuned["kernel_gflops"] / 1e3 / peaks["dfma_tflops"],
+                         "traffic": None,
                          "kernel": "batch graph (one-column FlatTree-TS kernel + executor), FP64",
-                         "peak_source": "152 SMs x 4 FP64 flop/clk x 2.070 GHz (unit counts and max clock)",
-                         "fp32_frac": fp32["kernel_gflops"] / 1e3 / FP32_PEAK_TFLOPS,
-                         "fp32_peak": FP32_PEAK_TFLOPS},
+                         "peak_source": "measured in this run: FP64 FMA probe, of measured",
+                         "fp32_frac": fp32["kernel_gflops"] / 1e3 / peaks["ffma_tflops"],
+                         "fp32_peak": peaks["ffma_tflops"], "fp32_peak_source": "measured: FP32 FMA probe"},
             "detail": {"tuned": tuned, "fixed_nb64_ib16_greedy": fixed, "fp32_tuned": fp32,
                        "speedup_tuned_vs_fixed": tuned["gflops"] / fixed["gflops"],
                        "tuning_seconds": t_tune,
                        "classes": [{k: c[k] for k in ("n", "m_lo", "m_hi", "nb", "ib", "tree", "BS", "gflops")}
                                    for c in db["classes"]]}}
-    emit(line)
-    return 0
+    return line
 
 
 # ------------------------------------------------------ per-tree comparison
-PLASMA_BS = (2, 4, 8, 16)
+def plasma_bs_candidates(tqr, p, q, tree, top=8):
+    """Domain sizes timed for PlasmaTree / PlasmaTree-TS at p x q tiles: the
+    `top` smallest unit-weight critical paths over BS = 1..p (ties: smaller
+    BS first), together with BS = 1 and BS = p."""
+    cps = sorted((tqr.tqr_critical_path(p, q, tree, bs), bs) for bs in range(1, p + 1))
+    return sorted({bs for _, bs in cps[:top]} | {1, p})
+
 
 
 def trees_main(args):
     """The tree sweep for every tree: GFLOP/s per (tree, q) and the measured
     makespan against the unit-weight critical path (Section 2.3 model),
     converted to time at one SM's FP64 rate (nb^3/3 flop per unit).
-    PlasmaTree and PlasmaTree-TS take the fastest measured BS.  Each entry is
-    the median of ``--steps`` factorizations after one warm-up."""
+    PlasmaTree and PlasmaTree-TS take the fastest measured BS of
+    plasma_bs_candidates (the critical-path model's best 8 and {1, p}).  Each
+    entry is the median of ``--steps`` factorizations after one warm-up."""
     import torch
     import paper_1104_4475_gb300 as tqr
     from paper_1104_4475_gb300 import build, workloads
     build.build()
     torch.cuda.set_device(0)
-    unit_s = NB ** 3 / 3.0 / (FP64_PEAK_TFLOPS * 1e12 / 152)
+    peaks = measure_peaks(tqr, torch)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    unit_s = NB ** 3 / 3.0 / (peaks["dfma_tflops"] * 1e12 / n_sm)
     trees = [("FlatTree-TS", tqr.FLAT_TS), ("FlatTree-TT", tqr.FLAT_TT), ("BinaryTree", tqr.BINARY),
              ("Fibonacci", tqr.FIBONACCI), ("Greedy", tqr.GREEDY), ("ASAP", tqr.ASAP),
              ("PlasmaTree", tqr.PLASMA), ("PlasmaTree-TS", tqr.PLASMA_TS)]
@@ -619,8 +743,8 @@ def trees_main(args):
         src = torch.from_numpy(np.ascontiguousarray(workloads.uniform(M, NB * q, SEED).T)).cuda().t()
         work = torch.empty_like(src.t()).t()
         for name, tree in trees:
-            bss = [b for b in PLASMA_BS if b <= M // NB] if tree in (tqr.PLASMA, tqr.PLASMA_TS) else [1]
-            best = None
+            bss = plasma_bs_candidates(tqr, M // NB, q, tree) if tree in (tqr.PLASMA, tqr.PLASMA_TS) else [1]
+            best, tried = None, {}
             for BS in bss:
                 times, h = [], None
                 for rep in range(args.steps + 1):
@@ -636,13 +760,15 @@ def trees_main(args):
                 cp = h.info()["critical_path"]
                 h.free()
                 t = statistics.median(times)
+                tried[BS] = 1e3 * t
                 if best is None or t < best["ms"] / 1e3:
                     best = {"BS": BS, "ms": 1e3 * t, "gflops": flops(M, NB * q) / t / 1e9,
                             "critical_path_units": cp, "cp_bound_ms": 1e3 * cp * unit_s,
                             "makespan_over_cp_bound": t / (cp * unit_s)}
+            if len(bss) > 1:
+                best["ms_per_BS"] = tried
             if args.trace_cp:
-                best.update(traced_critical_path(tqr, work, src, tree, best["BS"],
-                                                 torch.cuda.get_device_properties(0).multi_processor_count))
+                best.update(traced_critical_path(tqr, work, src, tree, best["BS"], n_sm))
             out.setdefault(name, {})[str(q)] = best
         del src, work
     sweep = {name: workload_flops() / sum(v[str(q)]["ms"] / 1e3 for q in QS) / 1e9 for name, v in out.items()}
@@ -650,8 +776,10 @@ def trees_main(args):
             "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "FP64 tree sweep for every tree: m=16384 (p=64), nb=256, ib=32, n=256q, "
-                                   "q in {1,2,4,8,16,32,64}, U[-0.5,0.5]; PlasmaTree BS measured over "
-                                   "{2,4,8,16}", "l2": "256 MiB flush write before each factorization"},
+                                   "q in {1,2,4,8,16,32,64}, U[-0.5,0.5]; PlasmaTree and PlasmaTree-TS BS "
+                                   "measured over the critical-path model's 8 best BS and {1, p}",
+                       "l2": "256 MiB flush write before each factorization"},
+            "measured_peaks": peaks,
             "best_tree": max(sweep, key=sweep.get), "sweep_gflops": sweep, "per_tree": out,
             "unit_ms": 1e3 * unit_s, "seconds": time.perf_counter() - t_all}
     emit(line)
@@ -679,6 +807,11 @@ def traced_critical_path(tqr, work, src, tree, BS, n_sm):
 
 # ------------------------------------------------------- learned cost model
 def costmodel_main(args):
+    emit(costmodel_line(args))
+    return 0
+
+
+def costmodel_line(args):
     """Trains the cost-model network on the GPU (the library's forward,
     backward and Adam kernels) from the stored executor timings, then scores
     its pick on the held-out shapes against the exhaustive best, the fixed
@@ -722,8 +855,7 @@ def costmodel_main(args):
             "detail": {"fp64": fp64, "split_tf32": lp, "test_rmse_log_seconds": rmse,
                        "train_seconds": train_s, "train_steps_per_s": steps / train_s,
                        "final_train_loss": losses[-1][1]}}
-    emit(line)
-    return 0
+    return line
 
 
 def main():
@@ -738,7 +870,13 @@ def main():
                          "costmodel: train and score the learned cost model")
     ap.add_argument("--cost-data", default=None, help="executor timings CSV for --workload costmodel")
     ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
-    ap.add_argument("--tune-db", default=None, help="autotune database to load, or to write after tuning")
+    ap.add_argument("--tune-db", default=TUNE_DB,
+                    help="FP64 batch autotune database to load, or to write after tuning (default: the stored "
+                         "GB300 database; '' to tune afresh)")
+    ap.add_argument("--tune-db32", default=TUNE_DB32, help="the same for the FP32 batch")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="default workload: skip the least-squares, batched and cost-model measurements that "
+                         "follow the sweep")
     ap.add_argument("--tune-sample", type=int, default=32, help="matrices per size class when tuning")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")

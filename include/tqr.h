@@ -408,6 +408,20 @@ int tqr_device_graph(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int
                      int64_t task_cap, int64_t* ntasks, int32_t* src, int32_t* dst, int64_t edge_cap,
                      int64_t* nedges);
 
+/* Peak-rate probes: the roofline denominators of the library's kernels,
+ * measured on the GPU that runs them (measurement support; the paper has no
+ * counterpart).  Enqueues on `stream` one launch that keeps every SM busy
+ * with independent chains of one kind of instruction for `iters` iterations
+ * and sets *flops (host) to the flops that launch performs; time the launch
+ * with events to get the rate.  kind: TQR_PEAK_DFMA (FP64 fma, the FP64
+ * kernels' arithmetic), TQR_PEAK_DMMA (FP64 mma.sync m8n8k4), TQR_PEAK_FFMA
+ * (FP32 fma), TQR_PEAK_TF32 (TF32 mma.sync m16n8k8 with FP32 accumulation).
+ * The first call on a device allocates one word of device memory that the
+ * library keeps until exit.  Errors: -1 kind, -2 iters < 1, -4 flops NULL,
+ * TQR_ERR_CUDA, TQR_ERR_NOMEM. */
+enum { TQR_PEAK_DFMA = 0, TQR_PEAK_DMMA = 1, TQR_PEAK_FFMA = 2, TQR_PEAK_TF32 = 3 };
+int tqr_peak_probe(int kind, int64_t iters, void* stream, double* flops);
+
 /* Test support for failure detection (the paper has no counterpart).
  * tqr_set_timeout_ms: limit, in milliseconds, for any single device wait of
  * later launches (ms <= 0 restores the default, which scales with the

@@ -46,7 +46,18 @@ static cudaError_t upload_graph(const Graph& g, DevGraphOwner& o) {
     if ((e = upload(&o.d.succ_ptr, g.succ_ptr)) != cudaSuccess) return e;
     if ((e = upload(&o.d.succ, g.succ)) != cudaSuccess) return e;
     if ((e = upload(&o.d.indeg, g.indeg)) != cudaSuccess) return e;
-    if ((e = upload(&o.d.ready, g.ready)) != cudaSuccess) return e;
+    // The initially ready tasks, high-priority ones first (program order kept).
+    std::vector<int32_t> ready;
+    ready.reserve(g.ready.size());
+    for (int32_t t : g.ready)
+        if (g.tasks[t].kind & kHighPriority) ready.push_back(t);
+    o.d.nready_hi = static_cast<int32_t>(ready.size());
+    for (int32_t t : g.ready)
+        if (!(g.tasks[t].kind & kHighPriority)) ready.push_back(t);
+    o.d.n_hi = 0;
+    for (const DevTask& x : g.tasks)
+        if (x.kind & kHighPriority) ++o.d.n_hi;
+    if ((e = upload(&o.d.ready, ready)) != cudaSuccess) return e;
     o.d.ntasks = static_cast<int32_t>(g.tasks.size());
     o.d.nready = static_cast<int32_t>(g.ready.size());
     o.d.nedges = static_cast<int64_t>(g.succ.size());
@@ -216,7 +227,7 @@ static cudaError_t alloc_state(ExecState& s, int32_t cap, int32_t* status) {
     const size_t n = std::max<int32_t>(1, cap);
     if ((e = cudaMalloc(&s.deps, n * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&s.queue, n * sizeof(int32_t))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.ctr, 2 * sizeof(uint32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.ctr, 4 * sizeof(uint32_t))) != cudaSuccess) return e;
     s.status = status;
     s.capacity = cap;
     return cudaSuccess;
@@ -349,7 +360,7 @@ struct tqr_factors {
 namespace tqr {
 DevGraph graph_for_launch(const DevGraph& g) {
     DevGraph x = g;
-    if (g_fault.exchange(0) == 1) x.nready = 0;      // one launch consumes the injection
+    if (g_fault.exchange(0) == 1) x.nready = x.nready_hi = 0;   // one launch consumes the injection
     return x;
 }
 }  // namespace tqr
@@ -667,11 +678,11 @@ int tqr_get_trace(tqr_factors* f, int64_t* out, int64_t cap, int64_t* count) {
         for (int64_t t = 0; t < nt; ++t) {
             const DevTask& x = P.g.tasks[t];
             int64_t* o = out + 8 * t;
-            o[0] = x.kind & 0xff;
+            o[0] = x.kind & kKindMask;
             o[1] = x.i;
             o[2] = x.piv;
             o[3] = x.k;
-            const int kind = x.kind & 0xff;
+            const int kind = x.kind & kKindMask;
             if (kind == GEQRT || kind == TTQRT || kind == TSQRT) {
                 // Whole panel: -1.  Block b of a split panel: b << 32 | c_lo << 16 | c_hi,
                 // [c_lo, c_hi) the columns it factors (the block's) or updates.
@@ -932,7 +943,7 @@ int tqr_device_graph(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int
         for (size_t x = 0; x < g.tasks.size(); ++x) {
             const DevTask& d = g.tasks[x];
             int32_t* o = tasks + 6 * x;
-            o[0] = d.kind & 0xff;
+            o[0] = d.kind & kKindMask;
             o[1] = d.i;
             o[2] = d.piv;
             o[3] = d.k;

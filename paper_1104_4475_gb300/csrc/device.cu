@@ -7,16 +7,29 @@ namespace tqr {
 
 namespace {
 
+// Dependency counters from the in-degrees; the initially ready tasks into
+// the two queues (ready[0, nready_hi) into the high-priority queue
+// queue[0, n_hi), the rest into queue[n_hi, ntasks)); every other slot -1.
 __global__ void init_kernel(int32_t* deps, const int32_t* indeg, int32_t* queue, const int32_t* ready,
-                            int nready, int ntasks, uint32_t* ctr, int32_t* status, int reset) {
+                            int nready, int nready_hi, int n_hi, int ntasks, uint32_t* ctr, int32_t* status,
+                            int reset) {
     const int stride = gridDim.x * blockDim.x;
+    const int nready_lo = nready - nready_hi;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += stride) {
         deps[t] = indeg[t];
-        queue[t] = (t < nready) ? ready[t] : -1;
+        int v = -1;
+        if (t < n_hi) {
+            if (t < nready_hi) v = ready[t];
+        } else if (t - n_hi < nready_lo) {
+            v = ready[nready_hi + (t - n_hi)];
+        }
+        queue[t] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr[0] = 0;
-        ctr[1] = static_cast<uint32_t>(nready);
+        ctr[1] = static_cast<uint32_t>(nready_hi);
+        ctr[2] = 0;
+        ctr[3] = static_cast<uint32_t>(nready_lo);
         if (reset) *status = 0;
     }
 }
@@ -149,12 +162,13 @@ cudaError_t launch_factor_exec(ExecParams P, const DevGraph& g, const ExecState&
     P.ctr = st.ctr;
     P.status = st.status;
     P.ntasks = g.ntasks;
+    P.n_hi = g.n_hi;
     const int nsm = device_sm_count();
     int ib = (g.ntasks + 255) / 256;
     if (ib > 4 * nsm) ib = 4 * nsm;
     if (ib < 1) ib = 1;
-    init_kernel<<<ib, 256, 0, s>>>(st.deps, g.indeg, st.queue, g.ready, g.nready, g.ntasks, st.ctr, st.status,
-                                  reset_status ? 1 : 0);
+    init_kernel<<<ib, 256, 0, s>>>(st.deps, g.indeg, st.queue, g.ready, g.nready, g.nready_hi, g.n_hi, g.ntasks,
+                                  st.ctr, st.status, reset_status ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (g.ntasks == 0) return cudaSuccess;

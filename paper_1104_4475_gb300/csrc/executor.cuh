@@ -395,6 +395,10 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
     }
 }
 
+template <int G, int MODE>
+__device__ void panel_update_range(const ExecParams& P, const Smem& S, const View& top, const View& bot, int i,
+                                   int k, int j0, int c_lo, int c_hi, bool staged);
+
 // Apply the reflectors of block j0 (factored and stored by panel_factor) to
 // columns [c_lo, c_hi) of the tile (pair).  staged: the block's V and tau are
 // still in shared memory from panel_factor in this CTA; otherwise they are
@@ -402,8 +406,7 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
 template <int G, int MODE, int PREC>
 __device__ void panel_update(const ExecParams& P, int i, int piv, int k, int j0, int c_lo, int c_hi, bool staged,
                              double* smem) {
-    constexpr int W = kThreads / G;
-    const int nb = P.nb, ib = P.ib;
+    const int nb = P.nb;
     const View bot = tile_view(P, i, k);
     const View top = (MODE == GE) ? bot : tile_view(P, piv, k);
     if (c_hi > bot.cv) c_hi = bot.cv;
@@ -413,6 +416,24 @@ __device__ void panel_update(const ExecParams& P, int i, int piv, int k, int j0,
         return;
     }
     const Smem S = layout<G>(P, smem);
+    if (G == 4 && c_hi - c_lo <= 32) {
+        // A narrow range (the look-ahead columns): 8 row groups of 32 columns,
+        // so that all 8 warps work (two per FP64 unit) rather than four.
+        Smem S8 = S;
+        S8.ldc = ldc_of(nb, 8);
+        panel_update_range<8, MODE>(P, S8, top, bot, i, k, j0, c_lo, c_hi, staged);
+        return;
+    }
+    panel_update_range<G, MODE>(P, S, top, bot, i, k, j0, c_lo, c_hi, staged);
+}
+
+// FP64 part of panel_update in the G-row-group layout (W = 256 / G columns
+// per pass), S laid out for it.
+template <int G, int MODE>
+__device__ void panel_update_range(const ExecParams& P, const Smem& S, const View& top, const View& bot, int i,
+                                   int k, int j0, int c_lo, int c_hi, bool staged) {
+    constexpr int W = kThreads / G;
+    const int nb = P.nb, ib = P.ib;
     if (!staged) {
         const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
         __syncthreads();
@@ -847,7 +868,7 @@ __device__ __forceinline__ void update_any(const ExecParams& P, const DevTask& T
 
 template <int G, int PREC>
 __device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
-    switch (T.kind & 0xff) {
+    switch (T.kind & kKindMask) {
         case GEQRT: panel_any<G, GE, PREC>(P, T, smem); break;
         case TTQRT: panel_any<G, TT, PREC>(P, T, smem); break;
         case TSQRT: panel_any<G, TS, PREC>(P, T, smem); break;
@@ -858,31 +879,79 @@ __device__ void run_task(const ExecParams& P, const DevTask& T, double* smem) {
     }
 }
 
-// Warp 0: decrement the successors of task t; push those that become ready.
+// Warp 0: decrement the successors of task t; push those that become ready,
+// each into the queue of its priority (slots reserved by one atomic per queue
+// and warp, then filled with release stores).
 __device__ void release_successors(const ExecParams& P, int t) {
     const int lane = threadIdx.x & 31;
     __threadfence();                      // the CTA's writes before the counters
     const int b = P.succ_ptr[t], e = P.succ_ptr[t + 1];
+    const unsigned below = (1u << lane) - 1u;
     for (int base = b; base < e; base += 32) {
         const int idx = base + lane;
         int s = -1;
-        bool ready = false;
+        bool ready = false, hi = false;
         if (idx < e) {
             s = P.succ[idx];
             ready = atom_add_acq_rel(&P.deps[s], -1) == 1;
+            if (ready) hi = (P.tasks[s].kind & kHighPriority) != 0;
         }
-        const unsigned mask = __ballot_sync(kFull, ready);
-        if (mask) {
+#pragma unroll
+        for (int qi = 0; qi < 2; ++qi) {
+            const bool mine = ready && (hi == (qi == 0));
+            const unsigned mask = __ballot_sync(kFull, mine);
+            if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             unsigned pos = 0;
-            if (lane == leader) pos = atomicAdd(&P.ctr[1], static_cast<unsigned>(__popc(mask)));
+            if (lane == leader) pos = atomicAdd(&P.ctr[qi == 0 ? 1 : 3], static_cast<unsigned>(__popc(mask)));
             pos = __shfl_sync(kFull, pos, leader);
-            if (ready) {
-                const unsigned rank = __popc(mask & ((1u << lane) - 1u));
-                if (pos + rank < static_cast<unsigned>(P.ntasks)) st_release(&P.queue[pos + rank], s);
+            if (mine) {
+                const unsigned slot = pos + __popc(mask & below);
+                const unsigned cap = (qi == 0) ? static_cast<unsigned>(P.n_hi)
+                                               : static_cast<unsigned>(P.ntasks - P.n_hi);
+                if (slot < cap) st_release(&P.queue[(qi == 0 ? 0 : P.n_hi) + slot], s);
                 else set_status(P.status, TQR_ERR_INTERNAL);
             }
         }
+    }
+}
+
+// Thread 0 of a CTA: the next task to run, or -1 when every task has been
+// taken or the run failed.  Each queue has a head (slots taken) and a tail
+// (slots reserved by pushers); a CTA takes slot `head` of the high-priority
+// queue when head < tail there, else of the other queue, by CAS on the head,
+// then reads the task (the pusher's store may still be in flight).  Every
+// wait is bounded by the run's time limit.
+__device__ int next_task(const ExecParams& P) {
+    const unsigned cap[2] = {static_cast<unsigned>(P.n_hi), static_cast<unsigned>(P.ntasks - P.n_hi)};
+    const int base[2] = {0, P.n_hi};
+    const uint64_t t0 = globaltimer();
+    unsigned it = 0;
+    for (;;) {
+        bool all_taken = true;
+        for (int qi = 0; qi < 2; ++qi) {
+            const unsigned h = static_cast<unsigned>(ld_acquire(reinterpret_cast<const int32_t*>(&P.ctr[2 * qi])));
+            if (h < cap[qi]) all_taken = false;
+            const unsigned tl = static_cast<unsigned>(ld_acquire(reinterpret_cast<const int32_t*>(&P.ctr[2 * qi + 1])));
+            if (h < tl && h < cap[qi] && atomicCAS(&P.ctr[2 * qi], h, h + 1u) == h) {
+                for (;;) {
+                    const int v = ld_acquire(&P.queue[base[qi] + h]);
+                    if (v >= 0) return v;
+                    if (ld_relaxed(P.status) != 0) return -1;
+                    if ((++it & 31u) == 0 && globaltimer() - t0 > P.timeout_ns) {
+                        set_status(P.status, TQR_ERR_TIMEOUT);
+                        return -1;
+                    }
+                }
+            }
+        }
+        if (all_taken) return -1;
+        if (ld_relaxed(P.status) != 0) return -1;
+        if ((++it & 31u) == 0 && globaltimer() - t0 > P.timeout_ns) {
+            set_status(P.status, TQR_ERR_TIMEOUT);
+            return -1;
+        }
+        __nanosleep(128);
     }
 }
 
@@ -892,27 +961,12 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(ExecParams P) {
     __shared__ int s_task;
     for (;;) {
         if (threadIdx.x == 0) {
-            int t = -1;
-            const unsigned slot = atomicAdd(&P.ctr[0], 1u);
-            if (slot < static_cast<unsigned>(P.ntasks)) {
-                const uint64_t t0 = globaltimer();
-                unsigned it = 0;
-                for (;;) {
-                    t = ld_acquire(&P.queue[slot]);
-                    if (t >= 0) break;
-                    if (ld_relaxed(P.status) != 0) break;
-                    if ((++it & 31u) == 0 && globaltimer() - t0 > P.timeout_ns) {
-                        set_status(P.status, TQR_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                if (t >= P.ntasks) {
-                    set_status(P.status, TQR_ERR_INTERNAL);
-                    t = -1;
-                }
-                if (t >= 0) __threadfence();
+            int t = next_task(P);
+            if (t >= P.ntasks) {
+                set_status(P.status, TQR_ERR_INTERNAL);
+                t = -1;
             }
+            if (t >= 0) __threadfence();
             s_task = t;
         }
         __syncthreads();

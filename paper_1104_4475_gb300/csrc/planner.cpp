@@ -401,11 +401,24 @@ bool split_panels(int nb, int ib) { return ib >= 8 && nb / ib >= 2; }
 // when split_panels(nb, ib), one task per block b of ib columns that factors
 // it, then tasks that apply it to the columns right of it: first the next
 // look-ahead columns (max(ib, 32) of them, which the next block's factor
-// waits for), then the rest in strips of W.  Writers of a tile are chained per
-// unit of gcd(ib, W) columns, in list order: a task depends on the last
-// writer of every unit it writes, and an update also on the panel task that
-// produced its reflectors (the factor of the panel's last block, which
-// follows every other task of the panel).
+// waits for), then the rest in strips of W.
+//
+// Writers of a tile are chained per cell of (row block, column unit) --
+// blocks of ib rows (all nb rows when panels stay whole) and units of
+// gcd(ib, W) columns -- in list order: a task depends on the last writer of
+// every cell it writes, and a task applying reflectors on the task that
+// formed them (for an update of another tile column: the factor task of the
+// panel's last block, which follows every other task of the panel).  Rows a
+// task writes: block b of GEQRT rows [b ib, nb) of its tile; of TTQRT rows
+// [0, (b+1) ib) of the zeroed tile and [b ib, (b+1) ib) of the pivot tile;
+// of TSQRT all rows of the zeroed tile and [b ib, (b+1) ib) of the pivot;
+// whole panels and update strips all rows.  So block b of an elimination
+// waits only for the blocks <= b of the tasks before it on those rows, and
+// the elimination tree proceeds as a wavefront over column blocks.  Panel
+// factor tasks, look-ahead updates and the updates of the next tile column
+// (k + 1) carry kHighPriority.  Readers
+// of a panel's reflectors do not wait for later writers of the other
+// triangle of the same tile (the reflectors' NODEP of Section 4).
 void build_factor_graph(int p, int q, int nb, int ib, int W, int n_cols_last,
                         const std::vector<TileTask>& tt, Graph& g) {
     const bool split = split_panels(nb, ib);
@@ -415,65 +428,83 @@ void build_factor_graph(int p, int q, int nb, int ib, int W, int n_cols_last,
         while (b) { const int r = a % b; a = b; b = r; }
         cu = a;
     }
-    const int umax = (nb + cu - 1) / cu;
+    const int rbs = split ? ib : nb;                  // rows per row block
+    const int umax = (nb + cu - 1) / cu, rmax = (nb + rbs - 1) / rbs;
+    const int cells = umax * rmax;
     auto cols_of = [&](int j) { return (j == q - 1) ? n_cols_last : nb; };
     const size_t ntile = static_cast<size_t>(p) * q;
-    std::vector<int32_t> last(ntile * umax, -1), prod(ntile * 2, -1);
-    auto L = [&](int r, int c, int u) -> int32_t& {
-        return last[(static_cast<size_t>(c) * p + r) * umax + u];
+    std::vector<int32_t> last(ntile * cells, -1), prod(ntile * 2, -1);
+    auto L = [&](int r, int c, int rb, int u) -> int32_t& {
+        return last[(static_cast<size_t>(c) * p + r) * cells + static_cast<size_t>(rb) * umax + u];
     };
     g.tasks.clear();
     std::vector<std::pair<int32_t, int32_t>> edges;
     edges.reserve(tt.size() * 4);
     std::vector<int32_t> deps;
-    deps.reserve(2 * umax + 4);
+    deps.reserve(2 * cells + 4);
     auto add_edges = [&](int32_t t) {
         std::sort(deps.begin(), deps.end());
         for (size_t a = 0; a < deps.size(); ++a)
             if (deps[a] >= 0 && (a == 0 || deps[a] != deps[a - 1])) edges.push_back({deps[a], t});
         deps.clear();
     };
-    // Task t writes columns [c0, c1) of tile column c in tile rows r0 (and r1 >= 0).
-    auto writes = [&](int32_t t, int r0, int r1, int c, int c0, int c1) {
+    // Task t writes rows [r0, r1) of columns [c0, c1) of tile (tr, tc).
+    auto writes = [&](int32_t t, int tr, int tc, int r0, int r1, int c0, int c1) {
         const int u0 = c0 / cu, u1 = (c1 + cu - 1) / cu;
-        for (int u = u0; u < u1; ++u) {
-            deps.push_back(L(r0, c, u));
-            L(r0, c, u) = t;
-            if (r1 >= 0) {
-                deps.push_back(L(r1, c, u));
-                L(r1, c, u) = t;
+        const int b0 = r0 / rbs, b1 = (r1 + rbs - 1) / rbs;
+        for (int rb = b0; rb < b1; ++rb)
+            for (int u = u0; u < u1; ++u) {
+                deps.push_back(L(tr, tc, rb, u));
+                L(tr, tc, rb, u) = t;
             }
-        }
     };
     auto push = [&](int32_t kind, int i, int piv, int k, int j, int strip) {
         const int32_t t = static_cast<int32_t>(g.tasks.size());
         g.tasks.push_back({kind, i, piv, k, j, strip});
         return t;
     };
+    // Rows block b of a panel of `kind` writes in the zeroed / factored tile
+    // (bottom) and in the pivot tile (top).
+    auto panel_rows = [&](int kind, int b, int* blo, int* bhi, int* tlo, int* thi) {
+        const int j0 = b * ib;
+        *blo = (kind == GEQRT) ? j0 : 0;
+        *bhi = (kind == TTQRT) ? std::min(nb, j0 + ib) : nb;
+        *tlo = j0;
+        *thi = std::min(nb, j0 + ib);
+    };
     const int la = ((ib > 32 ? ib : 32) + ib - 1) / ib * ib;   // look-ahead columns
     for (const TileTask& x : tt) {
         if (x.kind == GEQRT || x.kind == TTQRT || x.kind == TSQRT) {
-            const int r1 = (x.kind == GEQRT) ? -1 : x.piv;
+            const bool pair = x.kind != GEQRT;
             const int ncol = cols_of(x.k);
             int32_t sink;
             if (!split) {
-                sink = push(x.kind, x.i, x.piv, x.k, -1, 0);
-                writes(sink, x.i, r1, x.k, 0, ncol);
+                sink = push(x.kind | kHighPriority, x.i, x.piv, x.k, -1, 0);
+                writes(sink, x.i, x.k, 0, nb, 0, ncol);
+                if (pair) writes(sink, x.piv, x.k, 0, nb, 0, ncol);
                 add_edges(sink);
             } else {
                 int32_t prev = -1;
                 for (int b = 0; b < nb / ib; ++b) {
                     const int j0 = b * ib;
-                    const int32_t f = push(x.kind, x.i, x.piv, x.k, b, -1);
+                    int blo, bhi, tlo, thi;
+                    panel_rows(x.kind, b, &blo, &bhi, &tlo, &thi);
+                    const int32_t f = push(x.kind | kHighPriority, x.i, x.piv, x.k, b, -1);
                     deps.push_back(prev);
-                    if (j0 < ncol) writes(f, x.i, r1, x.k, j0, std::min(j0 + ib, ncol));
+                    if (j0 < ncol) {
+                        const int c1 = std::min(j0 + ib, ncol);
+                        writes(f, x.i, x.k, blo, bhi, j0, c1);
+                        if (pair) writes(f, x.piv, x.k, tlo, thi, j0, c1);
+                    }
                     add_edges(f);
                     prev = f;
                     for (int c0 = j0 + ib; c0 < ncol;) {
                         const int c1 = std::min(ncol, c0 == j0 + ib ? c0 + la : c0 + W);
-                        const int32_t u = push(x.kind, x.i, x.piv, x.k, b, c0 | (c1 << 16));
+                        const int32_t hp = (c0 == j0 + ib) ? kHighPriority : 0;   // the look-ahead part
+                        const int32_t u = push(x.kind | hp, x.i, x.piv, x.k, b, c0 | (c1 << 16));
                         deps.push_back(f);
-                        writes(u, x.i, r1, x.k, c0, c1);
+                        writes(u, x.i, x.k, blo, bhi, c0, c1);
+                        if (pair) writes(u, x.piv, x.k, tlo, thi, c0, c1);
                         add_edges(u);
                         c0 = c1;
                     }
@@ -484,10 +515,13 @@ void build_factor_graph(int p, int q, int nb, int ib, int W, int n_cols_last,
         } else {
             const int32_t pr = prod[(static_cast<size_t>(x.k) * p + x.i) * 2 + (x.kind == UNMQR ? 0 : 1)];
             const int ncol = cols_of(x.j);
+            const int32_t hp = (x.j == x.k + 1) ? kHighPriority : 0;      // feeds the next panel column
             for (int s = 0; s * W < ncol; ++s) {
-                const int32_t t = push(x.kind, x.i, x.piv, x.k, x.j, s);
+                const int32_t t = push(x.kind | hp, x.i, x.piv, x.k, x.j, s);
+                const int c0 = s * W, c1 = std::min(ncol, (s + 1) * W);
                 deps.push_back(pr);
-                writes(t, x.i, x.kind == UNMQR ? -1 : x.piv, x.j, s * W, std::min(ncol, (s + 1) * W));
+                writes(t, x.i, x.j, 0, nb, c0, c1);
+                if (x.kind != UNMQR) writes(t, x.piv, x.j, 0, nb, c0, c1);
                 add_edges(t);
             }
         }

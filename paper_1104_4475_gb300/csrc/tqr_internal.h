@@ -23,8 +23,12 @@ struct TileTask { int32_t kind, i, piv, k, j; };     // 0-based; piv/j = -1 when
 
 // One device task.  Update kernels are split into column strips: `strip`
 // selects columns [strip*W, strip*W + W) of tile column j (or of B).
+// Bit kHighPriority of `kind` sends the task, once ready, to the executor's
+// high-priority queue, which idle CTAs serve first.
+constexpr int32_t kHighPriority = 0x80;
+constexpr int32_t kKindMask = 0x7f;
 struct DevTask {
-    int32_t kind;    // Kind in bits 0-7; matrix of a batched factorization in bits 8-31
+    int32_t kind;    // Kind in bits 0-6, kHighPriority in bit 7; matrix of a batched factorization in bits 8-31
     int32_t i;       // row of the tile factored / zeroed / updated
     int32_t piv;     // pivot row (TT/TS kernels), else -1
     int32_t k;       // panel column
@@ -92,17 +96,19 @@ struct DevGraph {
     int32_t* succ_ptr = nullptr;
     int32_t* succ = nullptr;
     int32_t* indeg = nullptr;
-    int32_t* ready = nullptr;
+    int32_t* ready = nullptr;        // initially ready tasks: the high-priority ones first
     int32_t ntasks = 0, nready = 0;
+    int32_t n_hi = 0, nready_hi = 0; // tasks with kHighPriority; how many of them start ready
     int64_t nedges = 0;
 };
 
-// Mutable per-run state of the executor: dependency counters, ready queue,
-// queue head/tail and the status word.
+// Mutable per-run state of the executor: dependency counters, ready queues,
+// their heads/tails and the status word.  queue[0, n_hi) is the high-priority
+// queue, queue[n_hi, ntasks) the other one.
 struct ExecState {
     int32_t* deps = nullptr;
     int32_t* queue = nullptr;
-    uint32_t* ctr = nullptr;     // [0] head, [1] tail
+    uint32_t* ctr = nullptr;     // [0] head, [1] tail of the high queue; [2], [3] of the other
     int32_t* status = nullptr;
     int32_t capacity = 0;        // tasks the arrays can hold
 };
@@ -123,6 +129,7 @@ struct ExecParams {
     const DevTask* tasks; const int32_t* succ_ptr; const int32_t* succ;
     int32_t* deps; int32_t* queue; uint32_t* ctr; int32_t* status;
     int32_t ntasks;
+    int32_t n_hi;                                // size of the high-priority queue (queue[0, n_hi))
     uint64_t timeout_ns;                         // limit for any single wait
     uint64_t* trace;                             // optional: 2 per task (start, duration | sm << 56)
     const MatDesc* mats;                         // batched factorization: per-matrix fields, else null

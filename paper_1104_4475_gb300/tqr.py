@@ -95,6 +95,7 @@ def lib():
             "tqr_critical_path": [i32, i32, i32, i32, pi64, pi32],
             "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
             "tqr_device_graph": [i64, i64, i32, i32, i32, i32, i32, pi32, i64, pi64, pi32, pi32, i64, pi64],
+            "tqr_peak_probe": [i32, i64, vp, ctypes.POINTER(ctypes.c_double)],
             "tqr_set_trace": [vp, i32],
             "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
                                    ctypes.POINTER(vp)],
@@ -589,6 +590,17 @@ def tqr_tasks(p, q, tree, BS=1):
                            fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), out.shape[0], ctypes.byref(cnt)),
            "tqr_tasks")
     return out[: cnt.value], fin[: cnt.value]
+
+
+PEAK_DFMA, PEAK_DMMA, PEAK_FFMA, PEAK_TF32 = range(4)
+
+
+def tqr_peak_probe(kind, iters, stream=None):
+    """Enqueue one peak-rate probe launch (see tqr.h) on `stream`; returns the
+    flops it performs.  Time it with CUDA events on the same stream."""
+    fl = ctypes.c_double(0.0)
+    _check(lib().tqr_peak_probe(int(kind), int(iters), _stream(stream), ctypes.byref(fl)), "tqr_peak_probe")
+    return fl.value
 
 
 def tqr_device_graph(m, n, nb, ib, tree, BS=1, strip=64):

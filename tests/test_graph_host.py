@@ -5,8 +5,11 @@ alone decides the order of conflicting memory accesses.  From the kernel
 semantics of every device task (what it writes and which reflectors it reads)
 these tests check, with the transitive closure of the graph:
 
-* every two tasks that write the same column of the same tile are ordered,
-  the earlier one in program order (the sequential algorithm) first;
+* every two tasks that write overlapping rows of the same column of a tile
+  are ordered, the earlier one in program order (the sequential algorithm)
+  first -- rows by the kernels' definitions: block b of GEQRT writes rows
+  b ib.. of its tile, of TTQRT rows ..(b+1) ib of the zeroed tile, of TSQRT
+  all its rows, and of both eliminations rows b ib..(b+1) ib of the pivot;
 * every task that applies reflectors runs after the task that formed them;
 * a panel split into blocks is exactly that: one factor task per block of ib
   columns and update tasks that cover the columns right of the block once.
@@ -40,8 +43,9 @@ def closure(n, edges):
 
 
 def accesses(tasks, m, n, nb, ib, strip):
-    """Per task: the (tile row, tile column, column) cells it writes, the
-    reflector blocks (class, i, k, b) it reads and those it forms."""
+    """Per task: the writes ((tile row, tile column, column), row_lo, row_hi)
+    it makes, the reflector blocks (class, i, k, b) it reads and those it
+    forms."""
     q = -(-n // nb)
 
     def ncol(j):
@@ -50,24 +54,29 @@ def accesses(tasks, m, n, nb, ib, strip):
     nblk = nb // ib
     out = []
     for kind, i, piv, k, j, st in tasks.tolist():
-        rows = [i] if kind in (tqr.GEQRT, tqr.UNMQR) else [i, piv]
         if kind in PANELS:
             cls = GE_CLASS if kind == tqr.GEQRT else EL_CLASS
-            if j < 0:                                   # the whole panel
+            if j < 0:                                   # the whole panel: every row
                 cols, vr, vw = range(ncol(k)), [], [(cls, i, k, b) for b in range(nblk)]
-            elif st < 0:                                # factor block j
-                cols = range(j * ib, min((j + 1) * ib, ncol(k)))
-                vr, vw = [], [(cls, i, k, j)]
-            else:                                       # apply block j to [c_lo, c_hi)
-                cols = range(st & 0xffff, st >> 16)
-                vr, vw = [(cls, i, k, j)], []
+                rows = [(i, 0, nb)] + ([] if kind == tqr.GEQRT else [(piv, 0, nb)])
+            else:
+                j0 = j * ib
+                bot = {tqr.GEQRT: (j0, nb), tqr.TTQRT: (0, j0 + ib), tqr.TSQRT: (0, nb)}[kind]
+                rows = [(i,) + bot] + ([] if kind == tqr.GEQRT else [(piv, j0, j0 + ib)])
+                if st < 0:                              # factor block j
+                    cols = range(j0, min(j0 + ib, ncol(k)))
+                    vr, vw = [], [(cls, i, k, j)]
+                else:                                   # apply block j to [c_lo, c_hi)
+                    cols = range(st & 0xffff, st >> 16)
+                    vr, vw = [(cls, i, k, j)], []
             tc = k
         else:
             cls = GE_CLASS if kind == tqr.UNMQR else EL_CLASS
             cols = range(st * strip, min((st + 1) * strip, ncol(j)))
             vr, vw = [(cls, i, k, b) for b in range(nblk)], []
+            rows = [(i, 0, nb)] + ([] if kind == tqr.UNMQR else [(piv, 0, nb)])
             tc = j
-        out.append(([(r, tc, c) for r in rows for c in cols], vr, vw))
+        out.append(([((r, tc, c), lo, hi) for r, lo, hi in rows for c in cols], vr, vw))
     return out
 
 
@@ -91,13 +100,13 @@ def test_device_graph_orders_every_conflict(m, n, nb, ib, tree, BS, strip):
     N = len(tasks)
     reach = closure(N, edges)
     acc = accesses(tasks, m, n, nb, ib, strip)
-    last_writer, former = {}, {}
+    writers, former = {}, {}
     for t, (cells, vr, vw) in enumerate(acc):
-        for cell in cells:
-            a = last_writer.get(cell)
-            if a is not None:
-                assert (reach[t] >> a) & 1, "writers %d and %d of %s are not ordered" % (a, t, cell)
-            last_writer[cell] = t
+        for cell, lo, hi in cells:
+            for a, alo, ahi in writers.get(cell, ()):
+                if alo < hi and lo < ahi:
+                    assert (reach[t] >> a) & 1, "writers %d and %d of rows of %s are not ordered" % (a, t, cell)
+            writers.setdefault(cell, []).append((t, lo, hi))
         for blk in vw:
             assert blk not in former, "reflector block %s formed twice" % (blk,)
             former[blk] = t
@@ -140,18 +149,24 @@ def test_split_panels_cover_their_tiles_once(m, n, nb, ib, tree, BS, strip):
 
 def test_elimination_starts_before_the_geqrt_finishes():
     """Greedy on a 4 x 1 tile matrix: TTQRT's first block waits for the
-    first blocks of both GEQRTs, not for their last blocks."""
+    first blocks of both GEQRTs, not for their last blocks, and so does the
+    update of the last column unit by TTQRT's first block (row block 0 of
+    that unit is final once GEQRT's first block has been applied to it)."""
     nb, ib = 64, 16
     tasks, edges = tqr.tqr_device_graph(4 * nb, nb, nb, ib, tqr.GREEDY, 1, 64)
     reach = closure(len(tasks), edges)
     idx = {tuple(r): t for t, r in enumerate(tasks.tolist())}
-    tt = [t for t, r in enumerate(tasks.tolist()) if r[0] == tqr.TTQRT and r[4] == 0 and r[5] == -1][0]
-    _, i, piv, k, _, _ = tasks[tt].tolist()
+    first_tt = [t for t, r in enumerate(tasks.tolist()) if r[0] == tqr.TTQRT][0]
+    _, i, piv, k, _, _ = tasks[first_tt].tolist()
+    tt_f0 = idx[(tqr.TTQRT, i, piv, k, 0, -1)]
+    tt_u0 = [t for t, r in enumerate(tasks.tolist())
+             if r[:5] == [tqr.TTQRT, i, piv, k, 0] and r[5] >= 0 and (r[5] >> 16) == nb][0]
     for row in (i, piv):
         first = idx[(tqr.GEQRT, row, -1, k, 0, -1)]
         last = idx[(tqr.GEQRT, row, -1, k, nb // ib - 1, -1)]
-        assert (reach[tt] >> first) & 1
-        assert not (reach[tt] >> last) & 1
+        for t in (tt_f0, tt_u0):
+            assert (reach[t] >> first) & 1
+            assert not (reach[t] >> last) & 1
 
 
 def test_device_graph_rejects_bad_arguments():
