@@ -858,16 +858,106 @@ def costmodel_line(args):
     return line
 
 
+# ------------------------------------------------------ profiling drivers
+def case_main(args):
+    """One factorization size, for profilers and quick timing: factors an
+    m x (nb q) matrix of U[-0.5, 0.5] entries (seed 1) with the given tree,
+    BS and update arithmetic, restoring the input before each repetition,
+    and prints the CUDA-event time and GFLOP/s of each.  With --trace the
+    repetitions after the first are traced and the last one is summarised
+    (trace.report: SM busy fraction, time per kernel kind, measured critical
+    path, the Section 4 model's prediction)."""
+    import torch
+    import paper_1104_4475_gb300 as tqr
+    from paper_1104_4475_gb300 import build, workloads, trace as ttrace
+    build.build()
+    n = args.nb * args.q
+    A0 = torch.from_numpy(np.ascontiguousarray(workloads.uniform(args.m, n, SEED).T)).cuda().t()
+    A = torch.empty_like(A0.t()).t()
+    tree = tqr.TREES[args.tree]
+    f, traced = None, False
+    for r in range(args.warmup + args.steps):
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f = tqr.tqr_factor_ex(A, args.nb, args.ib, tree, args.BS, args.precision, reuse=f)
+        e1.record()
+        tqr.tqr_sync(f)
+        t = e0.elapsed_time(e1) / 1e3
+        info = f.info()
+        print("%s m=%d n=%d nb=%d ib=%d tree=%s BS=%d prec=%d tasks=%d cp=%d: %.3f ms, %.1f GFLOP/s"
+              % ("warmup" if r < args.warmup else "rep", args.m, n, args.nb, args.ib, args.tree, args.BS,
+                 args.precision, info["n_device_tasks"], info["critical_path"], 1e3 * t, info["flops"] / t / 1e9),
+              flush=True)
+        if args.trace and not traced:
+            tqr.tqr_set_trace(f, True)                  # from the next factorization on
+            traced = r + 1 < args.warmup + args.steps
+    if traced:
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        for ln in ttrace.report(tqr.tqr_get_trace(f), tqr.tqr_get_edges(f), f.info(), n_sm):
+            print(ln)
+    f.free()
+    return 0
+
+
+def batch_case_main(args):
+    """One batched configuration, for profilers and quick timing: factors
+    --count matrices m x n (N(0,1)) with the given nb, ib and tree (FP64) or
+    the one-column FP32 kernel (--dtype f32), restoring the inputs before each
+    repetition, and prints the CUDA-event time, GFLOP/s and GFLOP/s per
+    matrix."""
+    import torch
+    import paper_1104_4475_gb300 as tqr
+    from paper_1104_4475_gb300 import build
+    build.build()
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(5)
+    src = [torch.randn(args.n, args.m, generator=g, dtype=dt, device="cuda").t() for _ in range(args.count)]
+    work = [torch.empty_like(x.t()).t() for x in src]
+    fl = args.count * 2.0 * args.n * args.n * (args.m - args.n / 3.0)
+    b = None
+    for r in range(args.warmup + args.steps):
+        for w, x in zip(work, src):
+            w.copy_(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if args.dtype == "f32":
+            b = tqr.tqr_factor_batched_f32(work, args.nb, reuse=b)
+        else:
+            b = tqr.tqr_factor_batched(work, args.nb, args.ib, tqr.TREES[args.tree], args.BS, reuse=b)
+        e1.record()
+        tqr.tqr_batch_sync(b)
+        t = e0.elapsed_time(e1) / 1e3
+        print("%s count=%d m=%d n=%d nb=%d %s tree=%s one_column=%d: %.3f ms, %.1f GFLOP/s, %.2f GFLOP/s per matrix"
+              % ("warmup" if r < args.warmup else "rep", args.count, args.m, args.n, args.nb, args.dtype, args.tree,
+                 b.info()["n_fused"], 1e3 * t, fl / t / 1e9, fl / args.count / t / 1e9), flush=True)
+    b.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "lstsq", "batched", "trees", "costmodel"],
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "lstsq", "batched", "trees", "costmodel", "case", "batch-case"],
                     help="sweep: FP64 tree sweep (default); lstsq: mixed-precision least squares; "
                          "batched: 4096 tall-skinny matrices in one launch; trees: the sweep for every tree; "
-                         "costmodel: train and score the learned cost model")
+                         "costmodel: train and score the learned cost model; case / batch-case: one size, "
+                         "timed per repetition (for profilers; --steps repetitions after --warmup)")
+    ap.add_argument("--m", type=int, default=M, help="case / batch-case: rows")
+    ap.add_argument("--q", type=int, default=8, help="case: tile columns (n = nb q)")
+    ap.add_argument("--n", type=int, default=128, help="batch-case: columns")
+    ap.add_argument("--nb", type=int, default=NB, help="case / batch-case: tile size")
+    ap.add_argument("--ib", type=int, default=IB, help="case / batch-case: inner blocking")
+    ap.add_argument("--tree", default="greedy", help="case / batch-case: tree name (tqr.TREES)")
+    ap.add_argument("--BS", type=int, default=1, help="case / batch-case: PlasmaTree domain size")
+    ap.add_argument("--precision", type=int, default=0, help="case: 0 FP64, 1 split-TF32, 2 TF32 updates")
+    ap.add_argument("--trace", action="store_true", help="case: trace and summarise the last repetition")
+    ap.add_argument("--count", type=int, default=152, help="batch-case: matrices")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="batch-case: FP64 or FP32")
     ap.add_argument("--cost-data", default=None, help="executor timings CSV for --workload costmodel")
     ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--tune-db", default=TUNE_DB,
@@ -889,6 +979,10 @@ def main():
     args = ap.parse_args()
     global _JSONL
     _JSONL = args.jsonl
+    if args.workload == "case":
+        return case_main(args)
+    if args.workload == "batch-case":
+        return batch_case_main(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -105,7 +105,7 @@ typedef struct {
     int64_t n_elims;       /* length of the elimination list               */
     int64_t n_tile_tasks;  /* kernel tasks (Algorithms 2/3)                */
     int64_t n_device_tasks;/* tasks after splitting updates into strips and
-                              panels into blocks (nb / ib >= 2, ib >= 8)     */
+                              panels into blocks (nb >= 128, nb / ib >= 2, ib >= 8)     */
     int64_t n_edges;       /* dependency edges of the device task graph    */
     int64_t critical_path; /* unit-weight critical path, units of nb^3/3    */
     double flops;          /* 2 n^2 (m - n/3), the LAPACK count (Section 2.2) */
@@ -486,6 +486,17 @@ int tqr_inject_fault(int kind);
  * streams without ordering between them, say -- race on the array and give
  * wrong results.  Host threads are serialized while a call prepares its work.
  * ------------------------------------------------------------------------- */
+/* Test support: the task graph tqr_factor_noalloc builds for these
+ * arguments (its own fixed-capacity builder, panels as whole tasks), built on
+ * the host for update strips of `strip` columns (16, 32 or 64), in the format
+ * of tqr_device_graph.  No GPU is needed and nothing is allocated.  Argument
+ * errors: -1 m, -2 n, -3 nb, -4 ib, -5 list, -6 count, -7 ts, -8 strip,
+ * -11 ntasks, -15 nedges NULL; TQR_ERR_INVALID_LIST, TQR_ERR_TOO_LARGE and
+ * TQR_ERR_CAPACITY as for the factorization. */
+int tqr_noalloc_graph(int64_t m, int64_t n, int nb, int ib, const int32_t* list, int64_t count, int ts,
+                      int strip, int32_t* tasks, int64_t task_cap, int64_t* ntasks, int32_t* src,
+                      int32_t* dst, int64_t edge_cap, int64_t* nedges);
+
 #define TQR_NOALLOC_SCRATCH_BYTES (4 << 20)
 #define TQR_NOALLOC_MAX_TASKS 65536
 #define TQR_NOALLOC_MAX_TILES 4096

@@ -71,19 +71,22 @@ __device__ __forceinline__ void set_status(int32_t* status, int code) {
 // ------------------------------------------------------------ smem layout
 struct Smem {
     double* Cs;    // strip: nb x W, leading dimension ldc
-    double* Vs;    // reflector block: nb x ib, leading dimension nb
+    double* Vs;    // reflector block: nb x ib, leading dimension ldv
     double* Ct;    // top rows: ib x max(W, ib), leading dimension ldt
     double* taus;  // ib
-    int ldc, ldt;
+    int ldc, ldt, ldv;
 };
 
 __host__ __device__ inline int round16(int x) { return (x + 15) / 16 * 16; }
 __host__ __device__ inline int ldc_of(int nb, int G) { return round16(nb) + (G % 16); }
+// Reflector columns 8 (mod 16) doubles apart: the two columns a half-warp of
+// the 8-lane helpers reads fall on disjoint shared-memory banks.
+__host__ __device__ inline int ldv_of(int nb) { return round16(nb) + 8; }
 
 __host__ __device__ inline int smem_doubles(int nb, int ib, int G) {
     const int W = kThreads / G;
     const int wt = W > ib ? W : ib;
-    return ldc_of(nb, G) * W + nb * ib + (ib + 1) * wt + ib;
+    return ldc_of(nb, G) * W + ldv_of(nb) * ib + (ib + 1) * wt + ib;
 }
 
 template <int G>
@@ -92,9 +95,10 @@ __device__ __forceinline__ Smem layout(const ExecParams& P, double* base) {
     Smem s;
     s.ldc = ldc_of(P.nb, G);
     s.ldt = P.ib + 1;
+    s.ldv = ldv_of(P.nb);
     s.Cs = base;
     s.Vs = s.Cs + s.ldc * W;
-    s.Ct = s.Vs + P.nb * P.ib;
+    s.Ct = s.Vs + s.ldv * P.ib;
     const int wt = W > P.ib ? W : P.ib;
     s.taus = s.Ct + s.ldt * wt;
     return s;
@@ -201,7 +205,7 @@ __device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int i
         const int jj = trans ? s : ib - 1 - s;
         const int j = j0 + jj;
         const double tau = S.taus[jj];
-        const double* v = S.Vs + jj * nb;
+        const double* v = S.Vs + jj * S.ldv;
         int rlo, rhi;   // own rows r in [rlo, rhi), r = g (mod G)
         double acc;
         if (MODE == GE) {
@@ -213,14 +217,13 @@ __device__ __forceinline__ void apply_block(const Smem& S, int nb, int j0, int i
             rhi = (MODE == TT) ? j + 1 : nb;
             acc = (g == 0) ? S.Ct[jj + c * S.ldt] : 0.0;
         }
-        double acc2 = 0.0;
+        // One accumulation chain: each FP64 instruction occupies its
+        // sub-partition's unit for as long as its latency, and the other warp
+        // on the same unit fills the gaps, so a second chain (and the add
+        // that joins the two) would only cost an instruction.
         int r = rlo;
-        for (; r + G < rhi; r += 2 * G) {
-            acc = fma(v[r], Cc[r], acc);
-            acc2 = fma(v[r + G], Cc[r + G], acc2);
-        }
-        if (r < rhi) acc = fma(v[r], Cc[r], acc);
-        acc = group_sum<G>(acc + acc2);
+        for (; r < rhi; r += G) acc = fma(v[r], Cc[r], acc);
+        acc = group_sum<G>(acc);
         const double w = tau * acc;
         if (MODE == GE) {
             if (g == (j & (G - 1))) Cc[j] -= w;
@@ -255,7 +258,7 @@ __device__ __forceinline__ void fb_range(int j, int nb, int* rlo, int* rhi) {
 template <int MODE>
 __device__ void fb_form(const Smem& S, int nb, int j0, int jj, int lane, int32_t* status) {
     const int j = j0 + jj;
-    double* v = S.Vs + jj * nb;
+    double* v = S.Vs + jj * S.ldv;
     int rlo, rhi;
     fb_range<MODE>(j, nb, &rlo, &rhi);
     double sig = 0.0;
@@ -282,8 +285,8 @@ __device__ void fb_form(const Smem& S, int nb, int j0, int jj, int lane, int32_t
 template <int MODE>
 __device__ __forceinline__ void fb_apply(const Smem& S, int nb, int j0, int jj, int cc, double tau, int lane) {
     const int j = j0 + jj;
-    const double* v = S.Vs + jj * nb;
-    double* u = S.Vs + cc * nb;
+    const double* v = S.Vs + jj * S.ldv;
+    double* u = S.Vs + cc * S.ldv;
     int rlo, rhi;
     fb_range<MODE>(j, nb, &rlo, &rhi);
     double acc = 0.0;
@@ -298,13 +301,46 @@ __device__ __forceinline__ void fb_apply(const Smem& S, int nb, int j0, int jj, 
     for (int r = rlo + lane; r < rhi; r += 32) u[r] = fma(-v[r], w, u[r]);
 }
 
+// Warp-level, 8 lanes per column (4 columns per warp): applies reflector jj
+// to column cc.  Lane g of a column group handles rows r = rlo + g (mod 8).
+// Lanes whose column does not exist (valid false) take part in the shuffles
+// and write nothing.
+template <int MODE>
+__device__ __forceinline__ void fb_apply8(const Smem& S, int nb, int j0, int jj, int cc, double tau, int g,
+                                          bool valid) {
+    const int j = j0 + jj;
+    const double* v = S.Vs + jj * S.ldv;
+    const int col = valid ? cc : jj;
+    double* u = S.Vs + col * S.ldv;
+    int rlo, rhi;
+    fb_range<MODE>(j, nb, &rlo, &rhi);
+    double acc = (g == 0) ? ((MODE == GE) ? u[j] : S.Ct[jj + col * S.ldt]) : 0.0;
+    for (int r = rlo + g; r < rhi; r += 8) acc = fma(v[r], u[r], acc);
+    acc = group_sum<8>(acc);
+    const double w = tau * acc;
+    if (!valid) return;
+    if (g == 0) {
+        if (MODE == GE) u[j] -= w;
+        else S.Ct[jj + cc * S.ldt] -= w;
+    }
+    for (int r = rlo + g; r < rhi; r += 8) u[r] = fma(-v[r], w, u[r]);
+}
+
+// FP64 on sm_103 runs one warp instruction per 64 cycles on each of the SM's
+// four sub-partitions, and a warp sharing its sub-partition with another busy
+// warp waits several times longer per dependent instruction.  So warp 0, which
+// carries the chain (apply reflector jj to column jj+1, form reflector jj+1),
+// has its sub-partition to itself (warp 4 idles), and the six warps on the
+// other sub-partitions apply reflector jj to the block's columns jj+2.., four
+// columns per warp pass, 8 lanes per column.  One block barrier per reflector.
 template <int MODE>
 __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* status) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    constexpr int kWarps = kThreads / 32;
+    static_assert(kThreads == 256, "factor_block assigns eight warps");
     if (warp == 0) fb_form<MODE>(S, nb, j0, 0, lane, status);
     __syncthreads();
+    const int hw = (warp < 4) ? warp - 1 : warp - 2;    // helper index 0..5 (warps 1-3, 5-7)
     for (int jj = 0; jj < ib; ++jj) {
         const double tau = S.taus[jj];
         if (warp == 0) {
@@ -313,8 +349,11 @@ __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* sta
                 __syncwarp();
                 fb_form<MODE>(S, nb, j0, jj + 1, lane, status);
             }
-        } else {
-            for (int cc = jj + 1 + warp; cc < ib; cc += kWarps - 1) fb_apply<MODE>(S, nb, j0, jj, cc, tau, lane);
+        } else if (warp != 4) {
+            for (int c0 = jj + 2 + 4 * hw; c0 < ib; c0 += 24) {
+                const int cc = c0 + (lane >> 3);
+                fb_apply8<MODE>(S, nb, j0, jj, cc, tau, lane & 7, cc < ib);
+            }
         }
         __syncthreads();
     }
@@ -339,10 +378,10 @@ template <int MODE>
 __device__ __forceinline__ void stage_panel_block(const Smem& S, const View& top, const View& bot, int nb, int j0,
                                                   int ib) {
     if (MODE == GE) {
-        load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
+        load_rect(S.Vs, S.ldv, 0, bot, j0, nb, j0, ib);
     } else {
         load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib);
-        load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
+        load_rect(S.Vs, S.ldv, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
     }
 }
 
@@ -373,10 +412,10 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
     factor_block<MODE>(S, nb, j0, ib, P.status);
     // Write the block back: R (and V) in place, tau to the handle.
     if (MODE == GE) {
-        store_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib, false);
+        store_rect(S.Vs, S.ldv, 0, bot, j0, nb, j0, ib, false);
     } else {
         store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, j0, ib, true);
-        store_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
+        store_rect(S.Vs, S.ldv, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib, MODE == TT);
     }
     for (int t = threadIdx.x; t < ib; t += kThreads) tau_out[j0 + t] = S.taus[t];
     if (PREC != 0) {
@@ -386,9 +425,9 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
         for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
             const int r = idx % nb, jj = idx / nb, j = j0 + jj;
             float v;
-            if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * nb]));
-            else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * nb]) : 0.0f;
-            else v = static_cast<float>(S.Vs[r + jj * nb]);
+            if (MODE == GE) v = (r < j) ? 0.0f : (r == j ? 1.0f : static_cast<float>(S.Vs[r + jj * S.ldv]));
+            else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * S.ldv]) : 0.0f;
+            else v = static_cast<float>(S.Vs[r + jj * S.ldv]);
             Vdst[r + static_cast<int64_t>(j) * nb] = v;
         }
         form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
@@ -437,8 +476,8 @@ __device__ void panel_update_range(const ExecParams& P, const Smem& S, const Vie
     if (!staged) {
         const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(k) * P.p + i) * nb;
         __syncthreads();
-        if (MODE == GE) load_rect(S.Vs, nb, 0, bot, j0, nb, j0, ib);
-        else load_rect(S.Vs, nb, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
+        if (MODE == GE) load_rect(S.Vs, S.ldv, 0, bot, j0, nb, j0, ib);
+        else load_rect(S.Vs, S.ldv, 0, bot, 0, (MODE == TT) ? j0 + ib : nb, j0, ib);
         for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
     }
     for (int c0 = c_lo; c0 < c_hi; c0 += W) {
@@ -488,10 +527,34 @@ __device__ __forceinline__ void panel_any(const ExecParams& P, const DevTask& T,
     }
 }
 
+// load_rect by asynchronous copies (cp.async, 8 bytes each; entries outside
+// the view are zero-filled without a read); the caller commits and waits.
+__device__ __forceinline__ void load_rect_async(double* dst, int ldd, int rbase, const View& v, int r0, int r1,
+                                                int c0, int nc) {
+    const int nr = r1 - r0;
+    if (nr <= 0) return;
+    for (int idx = threadIdx.x; idx < nr * nc; idx += kThreads) {
+        const int r = r0 + idx % nr;
+        const int c = idx / nr;
+        const bool in = r < v.rv && c0 + c < v.cv;
+        const double* src = in ? v.p + r + static_cast<int64_t>(c0 + c) * v.ld : v.p;
+        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + (r - rbase) + c * ldd));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(in ? 8 : 0) : "memory");
+    }
+}
+
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ----------------------------------------------------------------------------
 // Update kernels on one strip: UNMQR (GE), TTMQR (TT), TSMQR (TS).  The
 // reflectors come from tile (i,k); the strip is columns [strip*W, +W) of
-// tile column j (rows i and piv), or of the right-hand side B.
+// tile column j (rows i and piv), or of the right-hand side B.  Reflectors
+// are staged hb at a time (hb = 16 when 16 divides ib and ib >= 32, else ib):
+// with two groups in the nb x ib reflector buffer, the next group (its
+// reflectors, taus and, for TT/TS, the strip's top rows) arrives by
+// asynchronous copies while the current one is applied.
 // ----------------------------------------------------------------------------
 template <int G, int MODE>
 __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem) {
@@ -509,28 +572,52 @@ __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem)
         bot = tile_view(P, T.i, T.j);
         top = (MODE == GE) ? bot : tile_view(P, T.piv, T.j);
     }
-    const int vrows_hi = nb;
+    const bool dbl = ib >= 32 && ib % 16 == 0;
+    const int hb = dbl ? 16 : ib;                            // reflectors per staged group
+    const int ng = nb / hb;
+    // Group gi: reflectors j0 = gi*hb.. in buffer gi & 1 (Vs columns, taus and Ct rows shifted by hb).
+    auto stage = [&](int gi) {
+        const int j0 = gi * hb, buf = dbl ? (gi & 1) : 0;
+        double* vs = S.Vs + buf * hb * S.ldv;
+        const int lo = (MODE == GE) ? j0 : 0, hi = (MODE == TT) ? j0 + hb : nb;
+        load_rect_async(vs, S.ldv, 0, vt, lo, hi, j0, hb);
+        for (int t = threadIdx.x; t < hb; t += kThreads) {
+            const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(S.taus + buf * hb + t));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(tau_in + j0 + t) : "memory");
+        }
+        if (MODE != GE) load_rect_async(S.Ct + buf * hb, S.ldt, j0, top, j0, j0 + hb, c0, W);
+        async_commit();
+    };
     load_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W);
-    const int nblk = nb / ib;
-    for (int bb = 0; bb < nblk; ++bb) {
-        const int b = P.trans ? bb : nblk - 1 - bb;
-        const int j0 = b * ib;
-        __syncthreads();
-        if (MODE == GE) load_rect(S.Vs, nb, 0, vt, j0, vrows_hi, j0, ib);
-        else load_rect(S.Vs, nb, 0, vt, 0, (MODE == TT) ? j0 + ib : vrows_hi, j0, ib);
-        for (int t = threadIdx.x; t < ib; t += kThreads) S.taus[t] = __ldcg(tau_in + j0 + t);
-        if (MODE != GE) load_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W);
-        __syncthreads();
-        apply_block<G, MODE>(S, nb, j0, ib, P.trans, bot.cv - c0);
+    stage(P.trans ? 0 : ng - 1);
+    for (int gg = 0; gg < ng; ++gg) {
+        const int gi = P.trans ? gg : ng - 1 - gg;
+        const int j0 = gi * hb, buf = dbl ? (gi & 1) : 0;
+        __syncthreads();                                      // the other buffer is no longer read
+        if (dbl && gg + 1 < ng) {
+            stage(P.trans ? gi + 1 : gi - 1);
+            async_wait<1>();
+        } else {
+            async_wait<0>();
+        }
+        __syncthreads();                                      // group gi has landed for every thread
+        Smem Sg = S;
+        Sg.Vs = S.Vs + buf * hb * S.ldv;
+        Sg.taus = S.taus + buf * hb;
+        Sg.Ct = S.Ct + buf * hb;
+        apply_block<G, MODE>(Sg, nb, j0, hb, P.trans, bot.cv - c0);
         if (MODE != GE) {
             __syncthreads();
-            store_rect(S.Ct, S.ldt, j0, top, j0, j0 + ib, c0, W, false);
+            store_rect(Sg.Ct, S.ldt, j0, top, j0, j0 + hb, c0, W, false);
+        }
+        if (!dbl && gg + 1 < ng) {
+            __syncthreads();
+            stage(P.trans ? gi + 1 : gi - 1);
         }
     }
     __syncthreads();
     store_rect(S.Cs, S.ldc, 0, bot, 0, nb, c0, W, false);
 }
-
 
 // ----------------------------------------------------------------------------
 // Mixed precision (split-TF32 or TF32 updates, FP64 panels).
@@ -552,8 +639,8 @@ __device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout,
         const int r = idx % ib, c = idx / ib;
         double s = 0.0;
         if (r < c) {
-            const double* vr = S.Vs + r * nb;
-            const double* vc = S.Vs + c * nb;
+            const double* vr = S.Vs + r * S.ldv;
+            const double* vc = S.Vs + c * S.ldv;
             const int jr = j0 + r, jc = j0 + c;
             if (MODE == GE) {
                 s = vr[jc];                                  // tail of r . unit entry of c

@@ -338,3 +338,51 @@ extern "C" int tqr_factor_noalloc(double* A, int64_t m, int64_t n, int nb, int i
     // The launch resets the counters, queue, head/tail and *status first.
     return launch_factor_exec(P, graph_for_launch(g), st, G, smem, true, s) == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }
+
+// The task graph tqr_factor_noalloc builds for this problem, built on the
+// host with update strips of `strip` columns (no GPU, no allocation).
+extern "C" int tqr_noalloc_graph(int64_t m, int64_t n, int nb, int ib, const int32_t* list, int64_t count, int ts,
+                                 int strip, int32_t* tasks, int64_t task_cap, int64_t* ntasks, int32_t* src,
+                                 int32_t* dst, int64_t edge_cap, int64_t* nedges) {
+    if (m < 1) return -1;
+    if (n < 1 || n > m) return -2;
+    if (nb < 8 || nb > 256 || nb % 4 != 0) return -3;
+    if (ib < 1 || ib > 64 || nb % ib != 0) return -4;
+    if (!list && count > 0) return -5;
+    if (count < 0) return -6;
+    if (ts != 0 && ts != 1) return -7;
+    if (strip != 16 && strip != 32 && strip != 64) return -8;
+    if (!ntasks) return -11;
+    if (!nedges) return -15;
+    const int64_t p64 = (m + nb - 1) / nb, q64 = (n + nb - 1) / nb;
+    if (p64 * q64 > kMaxTiles) return TQR_ERR_TOO_LARGE;
+    if ((nb + strip - 1) / strip > kMaxStrips) return TQR_ERR_UNSUPPORTED;
+    const int p = static_cast<int>(p64), q = static_cast<int>(q64);
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = validate(p, q, list, count);
+    if (rc != TQR_OK) return rc;
+    Builder b(p, q, nb, strip, static_cast<int>(n - static_cast<int64_t>(q - 1) * nb), ts != 0);
+    rc = b.build(list, count);
+    if (rc != TQR_OK) return rc;
+    *ntasks = g_h.ntasks;
+    *nedges = g_h.nedges;
+    if (*ntasks > task_cap || *nedges > edge_cap) return TQR_ERR_CAPACITY;
+    if ((!tasks && *ntasks) || ((!src || !dst) && *nedges)) return TQR_ERR_CAPACITY;
+    for (int t = 0; t < g_h.ntasks; ++t) {
+        const DevTask& d = g_h.tasks[t];
+        int32_t* o = tasks + 6 * t;
+        o[0] = d.kind & kKindMask;
+        o[1] = d.i;
+        o[2] = d.piv;
+        o[3] = d.k;
+        o[4] = d.j;
+        o[5] = d.strip;
+    }
+    int64_t e = 0;
+    for (int t = 0; t < g_h.ntasks; ++t)
+        for (int32_t k = g_h.succ_ptr[t]; k < g_h.succ_ptr[t + 1]; ++k, ++e) {
+            src[e] = t;
+            dst[e] = g_h.succ[k];
+        }
+    return TQR_OK;
+}

@@ -395,7 +395,9 @@ static void finish_graph(const std::vector<std::pair<int32_t, int32_t>>& edges, 
         if (g.indeg[t] == 0) g.ready.push_back(static_cast<int32_t>(t));
 }
 
-bool split_panels(int nb, int ib) { return ib >= 8 && nb / ib >= 2; }
+// Tiles of fewer than 128 columns stay whole: their blocks are too small for
+// a task each to pay for its scheduling.
+bool split_panels(int nb, int ib) { return nb >= 128 && ib >= 8 && nb / ib >= 2; }
 
 // Updates are split into strips of W columns.  Panels are one task each, or,
 // when split_panels(nb, ib), one task per block b of ib columns that factors

@@ -96,6 +96,7 @@ def lib():
             "tqr_tasks": [i32, i32, i32, i32, pi32, pi64, i64, pi64],
             "tqr_device_graph": [i64, i64, i32, i32, i32, i32, i32, pi32, i64, pi64, pi32, pi32, i64, pi64],
             "tqr_peak_probe": [i32, i64, vp, ctypes.POINTER(ctypes.c_double)],
+            "tqr_noalloc_graph": [i64, i64, i32, i32, pi32, i64, i32, i32, pi32, i64, pi64, pi32, pi32, i64, pi64],
             "tqr_set_trace": [vp, i32],
             "tqr_factor_batched": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, pi32, pi32, pi32, vp,
                                    ctypes.POINTER(vp)],
@@ -590,6 +591,26 @@ def tqr_tasks(p, q, tree, BS=1):
                            fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), out.shape[0], ctypes.byref(cnt)),
            "tqr_tasks")
     return out[: cnt.value], fin[: cnt.value]
+
+
+def tqr_noalloc_graph(m, n, nb, ib, elims, ts=False, strip=64):
+    """The task graph tqr_factor_noalloc builds for these arguments, built on
+    the host: (tasks (ntasks, 6) int32, edges (nedges, 2) int32) as
+    tqr_device_graph returns them."""
+    el = np.ascontiguousarray(elims, dtype=np.int32).reshape(-1, 3)
+    p32 = ctypes.POINTER(ctypes.c_int32)
+    nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().tqr_noalloc_graph(m, n, nb, ib, el.ctypes.data_as(p32), el.shape[0], int(bool(ts)), strip, None, 0,
+                                 ctypes.byref(nt), None, None, 0, ctypes.byref(ne))
+    if rc not in (0, TQR_ERR_CAPACITY):
+        _check(rc, "tqr_noalloc_graph")
+    tasks = np.zeros((max(1, nt.value), 6), dtype=np.int32)
+    src = np.zeros(max(1, ne.value), dtype=np.int32)
+    dst = np.zeros(max(1, ne.value), dtype=np.int32)
+    _check(lib().tqr_noalloc_graph(m, n, nb, ib, el.ctypes.data_as(p32), el.shape[0], int(bool(ts)), strip,
+                                   tasks.ctypes.data_as(p32), tasks.shape[0], ctypes.byref(nt), src.ctypes.data_as(p32),
+                                   dst.ctypes.data_as(p32), src.shape[0], ctypes.byref(ne)), "tqr_noalloc_graph")
+    return tasks[: nt.value], np.stack([src[: ne.value], dst[: ne.value]], axis=1)
 
 
 PEAK_DFMA, PEAK_DMMA, PEAK_FFMA, PEAK_TF32 = range(4)

@@ -204,3 +204,22 @@ def model_prediction(trace, nb, strip, n, critical_path, n_cta, flops, ib=None):
     return {"units": T, "gamma_seq_gflops": gamma_seq / 1e9, "bound": "cp" if critical_path > T / n_cta else "work",
             "bound_units": bound_units, "gamma_pred_gflops": gamma_seq * T / bound_units / 1e9 if bound_units else 0.0,
             "predicted_ms": 1e3 * t_pred, "predicted_lapack_gflops": flops / t_pred / 1e9 if t_pred > 0 else 0.0}
+
+
+def report(tr, edges, info, n_sm):
+    """Lines summarising one traced factorization: SM busy fraction and time
+    per kernel kind, the measured critical path against the makespan, and the
+    Section 4 model's predicted rate with gamma_seq taken from the trace;
+    info is the handle's tqr_get_info dict."""
+    s = summary(tr, n_sm)
+    cp_ns, path = measured_critical_path(tr, edges)
+    model = model_prediction(tr, info["nb"], info["strip"], info["n"], info["critical_path"], n_sm,
+                             info["flops"], info.get("ib"))
+    return ["trace: makespan %.3f ms, SMs busy %.1f %%, busy ms per kind %s"
+            % (s["makespan_ms"], 100 * s["busy_fraction"], {k: round(v, 3) for k, v in s["busy_ms_per_kind"].items()}),
+            "trace: measured critical path %.3f ms over %d tasks (%.1f %% of the makespan)"
+            % (cp_ns / 1e6, len(path), 100 * cp_ns / 1e6 / s["makespan_ms"]),
+            "model: T = %.0f units, cp = %d units, P = %d, bound %s; gamma_seq %.2f GFLOP/s per CTA, "
+            "gamma_pred %.1f GFLOP/s, predicted %.3f ms (%.1f GFLOP/s in LAPACK flops)"
+            % (model["units"], info["critical_path"], n_sm, model["bound"], model["gamma_seq_gflops"],
+               model["gamma_pred_gflops"], model["predicted_ms"], model["predicted_lapack_gflops"])]

@@ -108,6 +108,42 @@ TREES = [(tqr.FLAT_TS, 1), (tqr.FLAT_TT, 1), (tqr.SAMEH_KUCK, 1), (tqr.BINARY, 1
          (tqr.GRASAP, 2), (tqr.PLASMA_TS, 1), (tqr.PLASMA_TS, 3), (tqr.PLASMA_TS, 10)]
 
 
+SPLIT_CASES = [(1400, 600, 128, 32, tqr.GREEDY, 1), (1400, 600, 128, 16, tqr.FLAT_TS, 1),
+               (1300, 520, 128, 32, tqr.PLASMA_TS, 3), (1200, 500, 128, 64, tqr.BINARY, 1),
+               (1100, 404, 128, 16, tqr.FIBONACCI, 1), (1536, 768, 256, 32, tqr.GREEDY, 1),
+               (1600, 530, 256, 32, tqr.PLASMA_TS, 2)]
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree,BS", SPLIT_CASES)
+def test_split_panels_against_the_oracle(m, n, nb, ib, tree, BS):
+    """Tiles of nb >= 128, whose panels run as one task per block of ib
+    columns plus look-ahead and trailing update tasks: R, V, Q^T b and every
+    tau element-wise against the oracle, ragged last tile row and column
+    included (the 404- and 530-column cases leave whole blocks of the last
+    tile column empty)."""
+    A = workloads.uniform(m, n, seed=m + n + ib)
+    b = workloads.rhs(m, 1, seed=7)[:, 0]
+    f, Aout = gpu_factor(A, nb, ib, tree, BS)
+    F = otq.factor(A, nb, ib, tree, BS)
+    tol = tol_for(A)
+    compare(Aout, F.A, np.abs(F.r()).max(), tol, "R and V")
+    bt = tqr.colmajor(b)
+    tqr.tqr_apply_qt(f, bt)
+    tqr.tqr_sync(f)
+    compare(tqr.to_numpy(bt)[:, 0], otq.apply_qt(F, b), np.linalg.norm(b), tol, "Q^T b")
+    p, q = -(-m // nb), -(-n // nb)
+    Tge = torch.zeros(p * q * ib * nb, dtype=torch.float64, device="cuda")
+    Tel = torch.zeros_like(Tge)
+    tqr.tqr_form_t(f, Tge, Tel)
+    tqr.tqr_sync(f)
+    Tge = Tge.cpu().numpy().reshape(q, p, nb, ib).transpose(1, 0, 3, 2)
+    Tel = Tel.cpu().numpy().reshape(q, p, nb, ib).transpose(1, 0, 3, 2)
+    compare(Tge, F.Tge, 1.0, tol, "T of GEQRT (tau on its diagonal)")
+    compare(Tel, F.Tel, 1.0, tol, "T of the eliminations")
+    check_targets(f, A, Aout)
+    f.free()
+
+
 @pytest.mark.parametrize("tree,BS", TREES)
 def test_every_tree_ragged(tree, BS):
     """300 x 130, nb 32, ib 8: 10 x 5 tiles with a ragged last tile row and

@@ -82,14 +82,15 @@ def accesses(tasks, m, n, nb, ib, strip):
 
 CASES = [
     # m, n, nb, ib, tree, BS, strip
-    (512, 256, 64, 16, tqr.GREEDY, 1, 64),
-    (700, 300, 64, 16, tqr.FLAT_TS, 1, 64),         # ragged rows and columns, TS kernels
+    (1024, 512, 128, 16, tqr.GREEDY, 1, 64),
+    (1400, 600, 128, 32, tqr.FLAT_TS, 1, 64),       # ragged rows and columns, TS kernels
     (1024, 384, 128, 32, tqr.PLASMA_TS, 2, 64),     # TS inside domains, TT merges
-    (600, 250, 48, 16, tqr.BINARY, 1, 32),
-    (256, 256, 64, 8, tqr.FIBONACCI, 1, 16),        # square
-    (520, 202, 64, 16, tqr.GREEDY, 1, 64),          # last tile column: 10 columns, 3 empty blocks
-    (512, 192, 64, 64, tqr.GREEDY, 1, 64),          # nb / ib = 1: panels stay whole
-    (384, 128, 64, 4, tqr.FLAT_TT, 1, 64),          # ib < 8: panels stay whole
+    (1200, 500, 128, 16, tqr.BINARY, 1, 32),
+    (512, 512, 128, 8, tqr.FIBONACCI, 1, 16),       # square
+    (1040, 404, 128, 16, tqr.GREEDY, 1, 64),        # last tile column: 20 columns, 6 empty blocks
+    (1200, 600, 128, 64, tqr.GREEDY, 1, 64),        # two blocks per tile
+    (768, 256, 128, 4, tqr.FLAT_TT, 1, 64),         # ib < 8: panels stay whole
+    (600, 250, 48, 16, tqr.BINARY, 1, 32),          # nb < 128: panels stay whole
     (1536, 512, 256, 32, tqr.GREEDY, 1, 64),        # the benchmark's tile shape
 ]
 
@@ -116,11 +117,40 @@ def test_device_graph_orders_every_conflict(m, n, nb, ib, tree, BS, strip):
             assert (reach[t] >> f) & 1, "task %d applies %s without waiting for task %d" % (t, blk, f)
 
 
+@pytest.mark.parametrize("m,n,nb,ib,tree,BS,strip", [c for c in CASES if c[4] != tqr.PLASMA_TS])
+def test_noalloc_graph_orders_every_conflict(m, n, nb, ib, tree, BS, strip):
+    """tqr_factor_noalloc's own graph builder (whole panels), under the same
+    checks, and with the same tile-level task list as the library's."""
+    p, q = -(-m // nb), -(-n // nb)
+    elims = tqr.tqr_elimination_list(p, q, tree, BS)
+    tasks, edges = tqr.tqr_noalloc_graph(m, n, nb, ib, elims, tree == tqr.FLAT_TS, strip)
+    assert (tasks[[k in PANELS for k in tasks[:, 0]], 4] == -1).all()
+    reach = closure(len(tasks), edges)
+    writers, former = {}, {}
+    for t, (cells, vr, vw) in enumerate(accesses(tasks, m, n, nb, ib, strip)):
+        for cell, lo, hi in cells:
+            for a, alo, ahi in writers.get(cell, ()):
+                if alo < hi and lo < ahi:
+                    assert (reach[t] >> a) & 1, "writers %d and %d of rows of %s are not ordered" % (a, t, cell)
+            writers.setdefault(cell, []).append((t, lo, hi))
+        for blk in vw:
+            former[blk] = t
+        for blk in vr:
+            assert (reach[t] >> former[blk]) & 1
+    tile = []
+    for kind, i, piv, k, j, st in tasks.tolist():
+        key = (kind, i, piv, k, -1 if kind in PANELS else j)
+        if not tile or tile[-1] != key:
+            tile.append(key)
+    want, _ = tqr.tqr_tasks(p, q, tree, BS)
+    assert tile == [tuple(x) for x in want.tolist()]
+
+
 @pytest.mark.parametrize("m,n,nb,ib,tree,BS,strip", CASES)
 def test_split_panels_cover_their_tiles_once(m, n, nb, ib, tree, BS, strip):
     tasks, _ = tqr.tqr_device_graph(m, n, nb, ib, tree, BS, strip)
     p, q = -(-m // nb), -(-n // nb)
-    split = ib >= 8 and nb // ib >= 2
+    split = nb >= 128 and ib >= 8 and nb // ib >= 2
     # Collapsing the device tasks gives the tile-level task list, in order.
     tile = []
     for kind, i, piv, k, j, st in tasks.tolist():
@@ -152,7 +182,7 @@ def test_elimination_starts_before_the_geqrt_finishes():
     first blocks of both GEQRTs, not for their last blocks, and so does the
     update of the last column unit by TTQRT's first block (row block 0 of
     that unit is final once GEQRT's first block has been applied to it)."""
-    nb, ib = 64, 16
+    nb, ib = 128, 32
     tasks, edges = tqr.tqr_device_graph(4 * nb, nb, nb, ib, tqr.GREEDY, 1, 64)
     reach = closure(len(tasks), edges)
     idx = {tuple(r): t for t, r in enumerate(tasks.tolist())}

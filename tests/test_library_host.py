@@ -156,6 +156,39 @@ def test_plasma_ts_critical_paths_match_oracle():
                 assert lists_equal(p, q, tqr.PLASMA_TS, BS)
 
 
+BENCH_QS = (1, 2, 4, 8, 16, 32, 64)
+
+
+@pytest.mark.parametrize("q", BENCH_QS)
+def test_bench_sweep_plans_match_oracle_at_p64(q):
+    """At the benchmark's p = 64: the list, task list, ASAP finish times,
+    zero times and critical path of the tree the bench runs at this q, bit
+    for bit against the oracle; and for PlasmaTree and PlasmaTree-TS the
+    lists and critical paths at every domain size the per-tree sweep times
+    (the critical-path model's 8 best BS and {1, p})."""
+    import bench
+    p = 64
+    name, bs = bench.SWEEP_TREES[q]
+    tree = tqr.TREES[name]
+    el = otrees.elimination_list(p, q, tree, bs)
+    otasks = odag.expand(p, q, el, otrees.ts_flags(tree, bs, el))
+    ofin, ocp = odag.simulate(otasks)
+    tasks, fin = tqr.tqr_tasks(p, q, tree, bs)
+    want = np.array([[KIND_MAP[k], i - 1, piv - 1 if piv else -1, kk - 1, j - 1 if j else -1]
+                     for (k, i, piv, kk, j) in otasks], dtype=np.int32).reshape(-1, 5)
+    assert np.array_equal(tasks, want)
+    assert np.array_equal(fin, np.array(ofin, dtype=np.int64))
+    cp, zt = tqr.tqr_critical_path(p, q, tree, bs, zero_time=True)
+    assert cp == ocp
+    ozt = odag.zero_times(otasks, ofin)
+    assert all(zt[i, k] == ozt.get((i + 1, k + 1), -1) for i in range(p) for k in range(q))
+    for t in (tqr.PLASMA, tqr.PLASMA_TS):
+        for BS in bench.plasma_bs_candidates(tqr, p, q, t):
+            el = otrees.elimination_list(p, q, t, BS)
+            assert lists_equal(p, q, t, BS), (q, t, BS)
+            assert tqr.tqr_critical_path(p, q, t, BS) == odag.critical_path(p, q, el, otrees.ts_flags(t, BS, el))
+
+
 def test_validator_agrees_with_oracle():
     rng = np.random.default_rng(0)
     p, q = 7, 3

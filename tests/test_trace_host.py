@@ -113,10 +113,10 @@ def test_model_prediction_on_a_trace_of_known_rate():
         assert r["predicted_lapack_gflops"] == pytest.approx(flops / (b * c), rel=1e-6)
 
 
-def test_profile_case_trace_report_on_a_synthetic_trace():
-    """The report that profile_case --trace prints, on a trace built from the
-    host task list with a chain of edges (every task after the previous)."""
-    from paper_1104_4475_gb300 import profile_case
+def test_trace_report_on_a_synthetic_trace():
+    """The report that bench.py --workload case --trace prints, on a trace
+    built from the host task list with a chain of edges (every task after
+    the previous)."""
     p, q, nb, strip, c = 6, 3, 64, 32, 500
     n = q * nb
     tr = _tile_trace(p, q, tqr.GREEDY, nb, strip, n)
@@ -127,7 +127,7 @@ def test_profile_case_trace_report_on_a_synthetic_trace():
     edges = np.stack([np.arange(len(tr) - 1), np.arange(1, len(tr))], axis=1)
     info = {"nb": nb, "n": n, "strip": strip, "critical_path": tqr.tqr_critical_path(p, q, tqr.GREEDY),
             "flops": 2.0 * n * n * (p * nb - n / 3.0)}
-    lines = profile_case.trace_report(tr, edges, info, 4)
+    lines = ttrace.report(tr, edges, info, 4)
     assert len(lines) == 3
     assert "(100.0 % of the makespan)" in lines[1]               # a chain: the path is everything
     assert "T = %d units" % (6 * p * q * q - 2 * q ** 3) in lines[2]

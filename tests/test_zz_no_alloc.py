@@ -75,6 +75,35 @@ def test_noalloc_matches_tqr_factor_on_two_calls(m, n, nb, ib, tree):
         assert np.abs(got_el - ref_tau_el).max() <= tol
 
 
+@pytest.mark.parametrize("m,n,nb,ib,tree", [(1024, 256, 64, 16, tqr.GREEDY), (700, 300, 48, 16, tqr.FLAT_TS),
+                                           (600, 250, 64, 8, tqr.BINARY)])
+def test_noalloc_matches_the_oracle(m, n, nb, ib, tree):
+    """R, V and every tau element-wise against the CPU oracle's factorization
+    with the same tree (not only against tqr_factor)."""
+    from oracle import tiled_qr as otq
+    p, q = -(-m // nb), -(-n // nb)
+    A = workloads.gaussian(m, n, seed=130)
+    F = otq.factor(A, nb, ib, tree)
+    At = tqr.colmajor(A)
+    tau_ge = torch.zeros(p * q * nb, dtype=torch.float64, device="cuda")
+    tau_el = torch.zeros_like(tau_ge)
+    status = torch.full((1,), -999, dtype=torch.int32, device="cuda")
+    rc = tqr.tqr_factor_noalloc(At, nb, ib, tqr.tqr_elimination_list(p, q, tree), tau_ge, tau_el, status,
+                                ts=(tree == tqr.FLAT_TS))
+    assert rc == 0, tqr.tqr_strerror(rc)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    tol = tol_for(A)
+    scale = np.abs(F.r()).max()
+    assert np.abs(tqr.to_numpy(At) - F.A).max() / scale <= tol
+
+    def taus(T):   # the oracle's T blocks carry tau on their diagonal
+        return np.array([[[T[i, k][r % ib, r] for r in range(nb)] for i in range(p)] for k in range(q)])
+
+    assert np.abs(tau_ge.cpu().numpy().reshape(q, p, nb) - taus(F.Tge)).max() <= tol
+    assert np.abs(tau_el.cpu().numpy().reshape(q, p, nb) - taus(F.Tel)).max() <= tol
+
+
 def test_noalloc_refuses_problems_beyond_its_scratch():
     A = tqr.colmajor(np.zeros((8, 8)))
     tau = torch.zeros(8, dtype=torch.float64, device="cuda")
