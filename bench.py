@@ -514,11 +514,11 @@ def next_rows(args):
 
 # ----------------------------------------------------- mixed-precision LS
 LS_M, LS_N, LS_NB, LS_IB = 65536, 4096, 256, 32
-# Tree for both arithmetic paths: Greedy.  PlasmaTree with TS kernels inside
-# domains of 32 tile rows factors this shape 5-7 % faster on GB300, but its
-# flat TS chains make c = Q^T b slower, and the whole mixed-precision solve
-# took 0.526 s against 0.492 s with Greedy.
-LS_TREE, LS_BS = "greedy", 1
+# Tree for both arithmetic paths: PlasmaTree with TS kernels inside domains of
+# 32 tile rows, the fastest of Greedy, PlasmaTree-TS(32) and PlasmaTree-TS(64)
+# on GB300 for both paths (whole solves: FP64 2.07 / 2.15 / 2.12 s,
+# split-TF32 0.405 / 0.439 / 0.436 s at kappa = 1e2).
+LS_TREE, LS_BS = "plasma_ts", 32
 LS_KAPPAS = (1e2, 1e6, 1e10)
 
 
@@ -549,7 +549,7 @@ def lstsq_line(args):
                 x = torch.zeros(LS_N, dtype=torch.float64, device="cuda")
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                info = tqr.tqr_lstsq(A, b, x, LS_NB, LS_IB, tqr.TREES[LS_TREE], LS_BS, prec, tol, maxit)
+                info = tqr.tqr_lstsq(A, b, x, LS_NB, LS_IB, tqr.TREES[args.ls_tree], args.ls_bs, prec, tol, maxit)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 if rep > 0:
@@ -580,7 +580,8 @@ def lstsq_line(args):
             "vs_baseline": None, "dtype": "f64+tf32x3", "data": "synthetic",
             "config": {"workload": "least squares A = U diag(sigma) V^T, m=65536, n=4096, sigma log-spaced "
                                    "1..1/kappa, b = A x + 1e-10 N(0,1); value at kappa=1e6",
-                       "nb": LS_NB, "ib": LS_IB, "tree": "%s(BS=%d)" % (LS_TREE, LS_BS), "kappas": list(LS_KAPPAS)},
+                       "nb": LS_NB, "ib": LS_IB, "tree": "%s(BS=%d)" % (args.ls_tree, args.ls_bs),
+                       "kappas": list(LS_KAPPAS)},
             "detail": detail}
     return line
 
@@ -964,6 +965,8 @@ def main():
                     help="FP64 batch autotune database to load, or to write after tuning (default: the stored "
                          "GB300 database; '' to tune afresh)")
     ap.add_argument("--tune-db32", default=TUNE_DB32, help="the same for the FP32 batch")
+    ap.add_argument("--ls-tree", default=LS_TREE, help="least squares: elimination tree of both paths")
+    ap.add_argument("--ls-bs", type=int, default=LS_BS, help="least squares: PlasmaTree domain size")
     ap.add_argument("--no-next-rows", action="store_true",
                     help="default workload: skip the least-squares, batched and cost-model measurements that "
                          "follow the sweep")

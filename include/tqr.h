@@ -223,8 +223,9 @@ void tqr_free(tqr_factors* f);
 /* The library caches one plan (elimination list, task graph on the device,
  * apply graphs) per distinct (m, n, nb, ib, tree, BS) or caller-given list it
  * has factored, so that later calls with the same arguments build nothing.
- * tqr_release_plans drops every cached plan that no live handle uses, frees
- * its device memory, and clears the host-side plans of batched calls; it
+ * tqr_release_plans frees the workspace tqr_lstsq keeps, drops every cached
+ * plan that no live handle uses, frees its device memory, and clears the
+ * host-side plans of batched calls; it
  * returns the number of device plans dropped (>= 0) or TQR_ERR_INTERNAL.
  * Live handles keep their own plan and stay valid; a later call with released
  * arguments rebuilds the plan.  Host entry point: it frees device memory, so
@@ -262,8 +263,12 @@ int tqr_factor_host_async(double* A_host, int64_t m, int64_t n, int nb, int ib, 
  * maxit steps in all.  In FP64 tol is only compared with the final backward
  * error (converged = 1 when tol = 0).  info (host, may be NULL) receives iteration counts,
  * final backward error and phase times.  Synchronizes `stream` before
- * returning.  Allocates device workspace (m*n + n*n doubles + vectors) for the
- * call.  Argument errors, checked before any device work: -k for argument k
+ * returning.  R^-1 and R^-T are applied by blocked substitution, never formed.
+ * Device workspace (a copy of A, m*n doubles, plus vectors) and the factor
+ * handle (with FP32 copies of the reflectors in low precision) stay allocated
+ * after the call and serve the next call with the same arguments from any
+ * host thread (a call made while another thread's call uses them allocates
+ * its own, freed on return); tqr_release_plans() frees them.  Argument errors, checked before any device work: -k for argument k
  * (1 A, 2 m, 3 n, 4 b, 5 x, 6 nb, 7 ib, 8 tree, 9 BS, 10 precision, 11 tol
  * negative, NaN or infinite, 12 maxit), with nb, ib, tree and BS under
  * tqr_factor's rules; TQR_ERR_CAPACITY as tqr_factor. */

@@ -964,6 +964,7 @@ int tqr_device_graph(int64_t m, int64_t n, int nb, int ib, int tree, int BS, int
 
 int tqr_release_plans(void) {
     try {
+        release_lstsq_cache();                          // its handle holds a plan
         int dropped = 0;
         {
             std::lock_guard<std::mutex> lk(g_plans_mu);

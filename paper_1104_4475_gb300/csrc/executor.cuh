@@ -556,14 +556,33 @@ __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group
 // reflectors, taus and, for TT/TS, the strip's top rows) arrives by
 // asynchronous copies while the current one is applied.
 // ----------------------------------------------------------------------------
+template <int GL, int MODE>
+__device__ void update_task_g(const ExecParams& P, const DevTask& T, const Smem& S, int c0);
+
 template <int G, int MODE>
 __device__ void update_task(const ExecParams& P, const DevTask& T, double* smem) {
-    constexpr int W = kThreads / G;
     const Smem S = layout<G>(P, smem);
+    const int c0 = T.strip * (kThreads / G);
+    if (P.B && P.nrhs - c0 <= 8) {
+        // A narrow right-hand side (Q^T b for a few vectors): one warp per
+        // column, 32 lanes over the rows, instead of four lanes per column.
+        Smem S32 = S;
+        S32.ldc = ldc_of(P.nb, 32);
+        update_task_g<32, MODE>(P, T, S32, c0);
+        return;
+    }
+    update_task_g<G, MODE>(P, T, S, c0);
+}
+
+// update_task in the layout of GL row groups (W = 256 / GL columns), S laid
+// out for it, strip starting at column c0.
+template <int GL, int MODE>
+__device__ void update_task_g(const ExecParams& P, const DevTask& T, const Smem& S, int c0) {
+    constexpr int G = GL;
+    constexpr int W = kThreads / G;
     const int nb = P.nb, ib = P.ib;
     const View vt = tile_view(P, T.i, T.k);
     const double* tau_in = ((MODE == GE) ? P.tau_ge : P.tau_el) + (static_cast<int64_t>(T.k) * P.p + T.i) * nb;
-    const int c0 = T.strip * W;
     View bot, top;
     if (P.B) {
         bot = rhs_view(P, T.i, 0);

@@ -158,6 +158,9 @@ uint64_t exec_timeout_ns(double flops);
 // task when tqr_inject_fault(1) is pending (one launch consumes it), so that
 // every wait of that launch runs out (capi.cpp).
 DevGraph graph_for_launch(const DevGraph& g);
+// Frees the workspace and factor handle tqr_lstsq keeps for its next call
+// (lstsq.cu).
+void release_lstsq_cache();
 // Batched FlatTree-TS for one tile column (q = 1): one CTA per matrix, the tile
 // in registers, R in shared memory.  A matrix of n <= 128 columns with n <= nb
 // and nb in {64, 128, 256} (nb >= its column class 32 / 64 / 128; FP64 with

@@ -67,25 +67,29 @@ template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float4; static constexpr int N = 4; };
 template <> struct Vec2<double> { using T = double2; static constexpr int N = 2; };
 
+// One accumulation chain: with 8 or more warps per sub-partition the other
+// warps hide the chain's latency, and joining several chains would cost
+// instructions (each FP64 instruction occupies the sub-partition's unit for
+// as long as a dependent one waits).
 template <typename Real, int RPT>
 __device__ __forceinline__ Real dot_chunk(const Real* __restrict__ u, const Real (&x)[RPT]) {
     using V = typename Vec2<Real>::T;
     constexpr int N = Vec2<Real>::N;
-    Real a[4] = {Real(0), Real(0), Real(0), Real(0)};     // four independent chains
+    Real a = Real(0);
 #pragma unroll
     for (int k = 0; k < RPT; k += N) {
         const V w = *reinterpret_cast<const V*>(u + k);
         if constexpr (N == 4) {
-            a[0] = fma(w.x, x[k], a[0]);
-            a[1] = fma(w.y, x[k + 1], a[1]);
-            a[2] = fma(w.z, x[k + 2], a[2]);
-            a[3] = fma(w.w, x[k + 3], a[3]);
+            a = fma(w.x, x[k], a);
+            a = fma(w.y, x[k + 1], a);
+            a = fma(w.z, x[k + 2], a);
+            a = fma(w.w, x[k + 3], a);
         } else {
-            a[(k / 2) & 1 ? 2 : 0] = fma(w.x, x[k], a[(k / 2) & 1 ? 2 : 0]);
-            a[(k / 2) & 1 ? 3 : 1] = fma(w.y, x[k + 1], a[(k / 2) & 1 ? 3 : 1]);
+            a = fma(w.x, x[k], a);
+            a = fma(w.y, x[k + 1], a);
         }
     }
-    return (a[0] + a[1]) + (a[2] + a[3]);
+    return a;
 }
 
 template <typename Real, int RPT>
@@ -118,14 +122,13 @@ __device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, 
                                          Real* __restrict__ u, Real* R, Real* s_tau, Real* tau_out,
                                          int32_t* status) {
     Real a = ge ? Real(0) : R[packed(jn, jn)];   // TS: read before lane 0 overwrites it
-    Real sq[4] = {Real(0), Real(0), Real(0), Real(0)};   // four independent chains
+    Real sig = Real(0);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int row = r0 + k;
-        if (!ge || row > jn) sq[k & 3] = fma(x[k], x[k], sq[k & 3]);
+        if (!ge || row > jn) sig = fma(x[k], x[k], sig);
         if (ge && row == jn) a = x[k];
     }
-    Real sig = (sq[0] + sq[1]) + (sq[2] + sq[3]);
     sig = group_sum(sig, G, gmask);
     if (ge) a = group_sum(a, G, gmask);
     Real tau = Real(0), scale = Real(0), beta = a;

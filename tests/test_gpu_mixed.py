@@ -134,6 +134,31 @@ def test_lstsq_fp64_backward_error_matches_lapack(n, nb):
     assert info_t["converged"] == 0
 
 
+def test_lstsq_reuses_its_workspace():
+    """The workspace kept for the next call gives the same solution on
+    repeated calls, also after a call of another shape replaced it and after
+    tqr_release_plans freed it.  (The refinement's dot products sum block
+    partials in arrival order, so agreement is to rounding, not bitwise; a
+    stale workspace would be far off.)"""
+    A, b, _ = workloads.ls_problem(2048, 256, 1e4, seed=8)
+    A2, b2, _ = workloads.ls_problem(1500, 200, 1e3, seed=9)
+    same = lambda u, v: np.linalg.norm(u - v) <= 1e-12 * np.linalg.norm(u)
+    tol = 2 * solve(A, b, 128, 32, tqr.TQR_FP64)[1]["backward_error"]
+    x1, i1, _ = solve(A, b, 128, 32, tqr.TQR_SPLIT_TF32, tol=tol)
+    x2, i2, _ = solve(A, b, 128, 32, tqr.TQR_SPLIT_TF32, tol=tol)
+    assert same(x1, x2) and i1["converged"] == i2["converged"] == 1
+    y1, _, _ = solve(A2, b2, 64, 16, tqr.TQR_FP64)
+    x3, _, _ = solve(A, b, 128, 32, tqr.TQR_SPLIT_TF32, tol=tol)
+    assert same(x1, x3)
+    assert tqr.tqr_release_plans() >= 0
+    x4, _, _ = solve(A, b, 128, 32, tqr.TQR_SPLIT_TF32, tol=tol)
+    assert same(x1, x4)
+    y2, _, _ = solve(A2, b2, 64, 16, tqr.TQR_FP64)
+    assert same(y1, y2)
+    xnp = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.linalg.norm(x1 - xnp) <= 1e4 * 1e-13 * np.linalg.norm(xnp)
+
+
 def test_lstsq_ill_conditioned_reports_honestly():
     """kappa = 1e10 with split-TF32: kappa * u_s >> 1, plain refinement cannot
     contract; the solver hands over to preconditioned CGLS and reports whether
