@@ -32,11 +32,15 @@ sys.path.insert(0, ROOT)
 
 M, NB, IB = 16384, 256, 32
 QS = (1, 2, 4, 8, 16, 32, 64)
-# Tree (and PlasmaTree domain size) per q: the fastest of every tree, with BS
-# over {2, 4, 8, 16}, in a per-tree sweep of this workload on GB300 (ties go to
-# Greedy); the paper's experiments likewise keep the best domain size.
-SWEEP_TREES = {1: ("greedy", 1), 2: ("greedy", 1), 4: ("greedy", 1), 8: ("greedy", 1), 16: ("fibonacci", 1),
-               32: ("plasma_ts", 16), 64: ("plasma_ts", 16)}
+# Tree (and PlasmaTree domain size) per q: the fastest of every tree in the
+# per-tree sweep of this workload on GB300 (`--workload trees`; PlasmaTree and
+# PlasmaTree-TS over the critical-path model's 8 best BS and {1, p}), with
+# Greedy kept where it is within about 1 % of the fastest (single timings: at
+# q <= 4 the differences were 0.2 ms at most); the paper's experiments
+# likewise keep the best domain size.  FlatTree-TS at q = 64 is PlasmaTree-TS
+# with one domain (BS = p), which timed the same.
+SWEEP_TREES = {1: ("greedy", 1), 2: ("greedy", 1), 4: ("greedy", 1), 8: ("plasma_ts", 8), 16: ("plasma_ts", 8),
+               32: ("plasma_ts", 18), 64: ("flat_ts", 1)}
 TREE_NAME = "tuned per q: " + ", ".join("q=%d %s%s" % (q, t, "(BS=%d)" % b if t.startswith("plasma") else "")
                                         for q, (t, b) in SWEEP_TREES.items())
 SEED = 1
@@ -49,12 +53,12 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12
 CPU_SAMPLE_QS = (1, 2, 4)
 REF_SAMPLE_QS = (1, 2)
 # DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of the q = 8 launch of this sweep
-# (5.602 GB for 1.3174e11 flop).  The traffic comes from re-staging reflector
-# blocks and strips per update task, so it grows with the number of strip
-# tasks, i.e. in proportion to the flops at fixed nb and ib; the sweep's
-# per-step traffic is this ratio times the sweep's flops.
-TRAFFIC_BYTES_PER_FLOP = 5.602e9 / 1.3174e11
+# dram__bytes_write.sum of one ncu capture of the q = 8 Greedy launch of this
+# sweep (2.727 + 2.635 GB for 1.3174e11 flop).  The traffic comes from
+# re-staging reflector blocks and strips per update task, so it grows with the
+# number of strip tasks, i.e. in proportion to the flops at fixed nb and ib;
+# the sweep's per-step traffic is this ratio times the sweep's flops.
+TRAFFIC_BYTES_PER_FLOP = 5.3618e9 / 1.3174e11
 
 
 def flops(m, n):
@@ -697,7 +701,9 @@ def batched_line(args):
             "roofline": {"bound": "alu", "achieved": tuned["kernel_gflops"] / 1e3, "peak": peaks["dfma_tflops"],
                          "unit": "TFLOP/s", "frac": tuned["kernel_gflops"] / 1e3 / peaks["dfma_tflops"],
                          "traffic": None,
-                         "kernel": "batch graph (one-column FlatTree-TS kernel + executor), FP64",
+                         "kernel": "ts1_all_kernel<double>: the whole batch in one persistent launch "
+                                   "(one-column FlatTree-TS; slots of 1024/512/256 threads pop matrices from "
+                                   "size-sorted queues), replayed from a CUDA graph with one memset node",
                          "peak_source": "measured in this run: FP64 FMA probe, of measured",
                          "fp32_frac": fp32["kernel_gflops"] / 1e3 / peaks["ffma_tflops"],
                          "fp32_peak": peaks["ffma_tflops"], "fp32_peak_source": "measured: FP32 FMA probe"},

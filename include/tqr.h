@@ -314,10 +314,13 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
  * (Proposition 2's flat tree; the batch supplies the parallelism), provided nb
  * is 64, 128 or 256 and at least n rounded up to 32 / 64 / 128; with FP64,
  * n in 65..128 needs nb = 128.  The results equal
- * tqr_factor's for the same (nb, TQR_FLAT_TS) up to rounding.  Other matrices of
- * the batch go to the task-graph executor in the same call; each kind is one
- * launch (one per (column class 32 / 64 / 128, tile height) pair in use, up
- * to nine, plus the executor), all on `stream`.
+ * tqr_factor's for the same (nb, TQR_FLAT_TS) up to rounding.  All such
+ * matrices of a batch run in ONE persistent launch: one CTA of 1024 threads
+ * per SM whose slots of 1024, 512 or 256 threads (the thread count of the
+ * matrix's class) pop matrices, largest first, from one queue per thread
+ * count.  The batch's other matrices go to the task-graph executor in a
+ * second launch after it; both on `stream`, after one memset of the batch's
+ * status and queue counters.
  *
  * tqr_factor_batched_f32: the same for FP32 matrices (all arithmetic FP32);
  * every matrix must satisfy the one-tile-column conditions above (FP32 also

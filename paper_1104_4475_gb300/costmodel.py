@@ -11,9 +11,15 @@ without timing every candidate.
 * Data: wall times of the executor itself (CUDA events around tqr_factor_ex),
   collected by :func:`collect`.
 
-Command line:
-  python -m paper_1104_4475_gb300.costmodel collect --shapes 120 --out timings.csv
-  python -m paper_1104_4475_gb300.costmodel evaluate --data timings.csv
+* Candidates: 22 FP64 configurations (nb 128/256, ib 16/32, the Greedy,
+  Fibonacci, binary, flat TS/TT, PlasmaTree and PlasmaTree-TS trees with BS
+  2..32) and 8 split-TF32 ones; shapes up to 65536 x 8192 and 2e11 flops.
+
+Command line (the stored GB300 sets: 100 training shapes of seed 11, 200
+held-out shapes of seed 23 outside them):
+  python -m paper_1104_4475_gb300.costmodel collect --shapes 100 --seed 11 --out timings.csv
+  python -m paper_1104_4475_gb300.costmodel collect --shapes 200 --seed 23 --exclude-seed 11 --out heldout.csv
+  python -m paper_1104_4475_gb300.costmodel evaluate --data timings.csv --heldout heldout.csv
 """
 
 import argparse
@@ -27,17 +33,21 @@ import numpy as np
 
 from . import tqr
 
-TREE_IDS = list(range(9))
-FP64_CONFIGS = [(nb, 32, tree, None) for nb in (128, 256)
-                for tree in (tqr.GREEDY, tqr.BINARY, tqr.FIBONACCI, tqr.FLAT_TT, tqr.FLAT_TS, tqr.PLASMA)]
-LP_CONFIGS = [(256, 32, tree, None) for tree in (tqr.GREEDY, tqr.BINARY, tqr.FIBONACCI, tqr.FLAT_TT, tqr.FLAT_TS,
-                                                 tqr.PLASMA)]
+TREE_IDS = list(range(10))                   # every generator of the library, PlasmaTree-TS included
+BS_TREES = (tqr.PLASMA, tqr.GRASAP, tqr.PLASMA_TS)
+# (nb, ib, tree, BS) of the FP64 candidates; BS is clipped to p.  ib takes both
+# values the low-precision path allows, BS spans a domain of 2 to 32 tiles.
+FP64_CONFIGS = ([(nb, ib, tree, 1) for nb in (128, 256) for ib in (16, 32)
+                 for tree in (tqr.GREEDY, tqr.FLAT_TS, tqr.FIBONACCI)]
+                + [(nb, 32, tree, 1) for nb in (128, 256) for tree in (tqr.BINARY, tqr.FLAT_TT)]
+                + [(256, 32, tqr.PLASMA, BS) for BS in (2, 8, 32)]
+                + [(256, 32, tqr.PLASMA_TS, BS) for BS in (8, 32)] + [(128, 32, tqr.PLASMA_TS, 32)])
+LP_CONFIGS = ([(256, ib, tree, 1) for ib in (16, 32) for tree in (tqr.GREEDY, tqr.FLAT_TS)]
+              + [(256, 32, tree, 1) for tree in (tqr.FIBONACCI, tqr.BINARY)]
+              + [(256, 32, tqr.PLASMA_TS, 32), (128, 32, tqr.GREEDY, 1)])
 DEFAULT = (256, 32, tqr.GREEDY, 1, 0)        # the configuration used without a model
-FEATURES = 22
-
-
-def plasma_bs(m, nb):
-    return max(1, -(-m // nb) // 8)
+FEATURES = 23
+VERSION = 2
 
 
 def features(m, n, nb, ib, tree, BS, prec):
@@ -50,7 +60,7 @@ def features(m, n, nb, ib, tree, BS, prec):
     flops = 2.0 * n * n * (m - n / 3.0)
     f = [math.log2(m) / 16, math.log2(n) / 16, math.log2(nb) / 8, ib / nb, math.log2(p) / 9, math.log2(q) / 9]
     f += [1.0 if tree == t else 0.0 for t in TREE_IDS]
-    f += [BS / p if tree in (tqr.PLASMA, tqr.GRASAP) else 0.0]
+    f += [BS / p if tree in BS_TREES else 0.0]
     f += [1.0 if prec == k else 0.0 for k in range(3)]
     f += [math.log2(flops) / 48, math.log2(cp * nb ** 3 / 3.0) / 48, math.log2(cp) / 12]
     assert len(f) == FEATURES
@@ -58,36 +68,40 @@ def features(m, n, nb, ib, tree, BS, prec):
 
 
 def configs_for(m, with_lp=True):
+    """Every candidate (nb, ib, tree, BS, precision) for m rows: 22 FP64 and
+    8 split-TF32 configurations."""
     out = []
-    for nb, ib, tree, _ in FP64_CONFIGS:
-        out.append((nb, ib, tree, plasma_bs(m, nb) if tree == tqr.PLASMA else 1, 0))
-    if with_lp:
-        for nb, ib, tree, _ in LP_CONFIGS:
-            out.append((nb, ib, tree, plasma_bs(m, nb) if tree == tqr.PLASMA else 1, 1))
+    for prec, grid in ((0, FP64_CONFIGS), (1, LP_CONFIGS if with_lp else [])):
+        for nb, ib, tree, BS in grid:
+            out.append((nb, ib, tree, min(BS, -(-m // nb)), prec))
     return out
 
 
-def random_shapes(count, seed, m_range=(4096, 65536), n_range=(256, 8192), max_flops=5e11):
-    """Log-uniform shapes with n <= m and at most max_flops LAPACK flops."""
+def random_shapes(count, seed, m_range=(4096, 65536), n_range=(256, 8192), max_flops=2e11, exclude=()):
+    """Log-uniform shapes with n <= m, at most max_flops LAPACK flops, none of
+    them in exclude (the training shapes, when drawing held-out ones)."""
     rng = np.random.default_rng(seed)
     out = []
+    exclude = set(exclude)
     while len(out) < count:
         m = int(2 ** rng.uniform(math.log2(m_range[0]), math.log2(m_range[1])))
         n = int(2 ** rng.uniform(math.log2(n_range[0]), math.log2(min(n_range[1], m))))
         m, n = m // 64 * 64, max(256, n // 64 * 64)
-        if n <= m and 2.0 * n * n * (m - n / 3.0) <= max_flops:
+        if n <= m and 2.0 * n * n * (m - n / 3.0) <= max_flops and (m, n) not in exclude:
             out.append((m, n))
     return out
 
 
-def collect(shapes, with_lp=True, log=None, seed=1, out=None):
+def collect(shapes, with_lp=True, log=None, seed=1, out=None, max_seconds=None):
     """Time every candidate configuration on each shape with CUDA events
     around tqr_factor_ex (the second of two runs, so the cached plan is
-    reused as in steady use); returns a list of records."""
+    reused as in steady use); returns a list of records.  With max_seconds,
+    stops after the first shape that ends past that much wall time."""
     import torch
     from . import build
     build.build()
     recs = []
+    t0 = time.time()
     g = torch.Generator(device="cuda").manual_seed(seed)
     for si, (m, n) in enumerate(shapes):
         src = (torch.rand(n, m, generator=g, dtype=torch.float64, device="cuda") - 0.5).t()
@@ -110,6 +124,8 @@ def collect(shapes, with_lp=True, log=None, seed=1, out=None):
         if out:
             save_records(recs, out)                    # after every shape: a cut-off run keeps its data
         del src, work
+        if max_seconds is not None and time.time() - t0 > max_seconds:
+            break
     return recs
 
 
@@ -157,14 +173,14 @@ class Model:
         return y.cpu().numpy().astype(np.float64) + self.ymu
 
     def to_json(self):
-        return {"version": 1, "features": FEATURES, "params": self.params.cpu().numpy().tolist(),
+        return {"version": VERSION, "features": FEATURES, "params": self.params.cpu().numpy().tolist(),
                 "mu": self.mu.tolist(), "sd": self.sd.tolist(), "ymu": self.ymu}
 
     @staticmethod
     def from_json(d):
-        if d.get("version") != 1 or d.get("features") != FEATURES:
-            raise ValueError("model file version %r with %r features; this code reads version 1 with %d"
-                             % (d.get("version"), d.get("features"), FEATURES))
+        if d.get("version") != VERSION or d.get("features") != FEATURES:
+            raise ValueError("model file version %r with %r features; this code reads version %d with %d"
+                             % (d.get("version"), d.get("features"), VERSION, FEATURES))
         import torch
         return Model(torch.tensor(d["params"], dtype=torch.float32, device="cuda"), np.array(d["mu"], np.float32),
                      np.array(d["sd"], np.float32), float(d["ymu"]))
@@ -263,6 +279,10 @@ def main(argv=None):
     c.add_argument("--shapes", type=int, default=120)
     c.add_argument("--seed", type=int, default=11)
     c.add_argument("--out", required=True)
+    c.add_argument("--exclude-seed", type=int, default=None,
+                   help="draw shapes outside those of this seed (and --exclude-count): held-out shapes")
+    c.add_argument("--exclude-count", type=int, default=100)
+    c.add_argument("--max-seconds", type=float, default=None)
     e = sub.add_parser("evaluate")
     e.add_argument("--data", required=True)
     e.add_argument("--heldout", default=None, help="separate held-out timings (train on all of --data)")
@@ -271,8 +291,9 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "collect":
         t0 = time.time()
-        recs = collect(random_shapes(a.shapes, a.seed), log=lambda s: print(s, file=sys.stderr, flush=True),
-                       out=a.out)
+        skip = random_shapes(a.exclude_count, a.exclude_seed) if a.exclude_seed is not None else ()
+        recs = collect(random_shapes(a.shapes, a.seed, exclude=skip),
+                       log=lambda s: print(s, file=sys.stderr, flush=True), out=a.out, max_seconds=a.max_seconds)
         print(json.dumps({"records": len(recs), "seconds": time.time() - t0}))
     else:
         recs = load_records(a.data)

@@ -292,16 +292,15 @@ struct tqr_batch {
     int64_t max_cp = 0;
     double flops = 0.0;
     cudaStream_t stream = nullptr;
-    // Matrices on the one-tile-column FlatTree-TS kernel, by (column class 32 / 64 / 128,
-    // tile height 64 / 128 / 256).
-    struct Ts1Class {
-        Ts1Desc* d = nullptr;
-        int count = 0, ncol = 0, h = 0;
-    } ts1[9];
+    // Matrices on the one-tile-column FlatTree-TS kernel: descriptors by
+    // thread count (1024, 512, 256), largest first within each, and the
+    // queues of the one persistent launch that runs them all.
+    Ts1Desc* ts1 = nullptr;
+    Ts1Phases ts1_ph{};
     int n_fused = 0;
     bool has_exec = false;
     ~tqr_batch() {
-        for (auto& c : ts1) cudaFree(c.d);
+        cudaFree(ts1);
         cudaFree(d_mats);
         cudaFree(tau_ge);
         cudaFree(tau_el);
@@ -998,10 +997,11 @@ int tqr_inject_fault(int kind) {
 }
 
 static int launch_batch(tqr_batch* b) {
-    if (cudaMemsetAsync(b->status, 0, sizeof(int32_t), b->stream) != cudaSuccess) return TQR_ERR_CUDA;
-    for (const auto& k : b->ts1)
-        if (launch_ts1(k.d, k.count, k.ncol, k.h, b->f32, b->tau_ge, b->tau_el, b->status, b->stream) != cudaSuccess)
-            return TQR_ERR_CUDA;
+    // status word and the persistent launch's three queue counters
+    if (cudaMemsetAsync(b->status, 0, 4 * sizeof(int32_t), b->stream) != cudaSuccess) return TQR_ERR_CUDA;
+    if (b->n_fused > 0 && launch_ts1_all(b->ts1, b->ts1_ph, b->f32, b->tau_ge, b->tau_el, b->status, b->status + 1,
+                                         b->stream) != cudaSuccess)
+        return TQR_ERR_CUDA;
     if (!b->has_exec) return TQR_OK;
     ExecParams P{};
     P.tau_ge = b->tau_ge;
@@ -1015,27 +1015,40 @@ static int launch_batch(tqr_batch* b) {
     return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }
 
-// Sorts the one-tile-column matrices of a batch into their column classes
-// (largest work first, so the hardware's in-order block dispatch balances
-// the SMs) and uploads their descriptors.
+// Sorts the one-tile-column matrices of a batch into the persistent launch's
+// queues: by thread count (1024 first), then largest work first, so that the
+// slots finish together; sizes the shared-memory quarters (a slot of nt
+// threads owns nt/256 of them) and uploads the descriptors.
 static int build_ts1(tqr_batch* b, const std::vector<Ts1Desc>& fused) {
-    std::vector<Ts1Desc> cls[9];
-    for (const Ts1Desc& d : fused) {
-        const int nc = ts1_ncol_class(d.n);
-        const int k = (nc == 32 ? 0 : (nc == 64 ? 1 : 2)) * 3 + (d.h == 64 ? 0 : (d.h == 128 ? 1 : 2));
-        cls[k].push_back(d);
-        b->ts1[k].ncol = nc;
-        b->ts1[k].h = d.h;
-        b->max_cp = std::max<int64_t>(b->max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
+    const int esz = b->f32 ? 4 : 8;
+    auto phase = [esz](const Ts1Desc& d) {
+        const int nt = ts1_threads(ts1_ncol_class(d.n), d.h, esz);
+        return nt == 1024 ? 0 : (nt == 512 ? 1 : 2);
+    };
+    std::vector<Ts1Desc> q(fused);
+    std::stable_sort(q.begin(), q.end(), [&](const Ts1Desc& x, const Ts1Desc& y) {
+        const int px = phase(x), py = phase(y);
+        if (px != py) return px < py;
+        return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
+    });
+    Ts1Phases ph{};
+    int quarter = 16;
+    for (int k = 0, at = 0; k < 3; ++k) {
+        ph.begin[k] = at;
+        while (at < static_cast<int>(q.size()) && phase(q[at]) == k) {
+            const Ts1Desc& d = q[at];
+            const int per = (1024 >> k) / 256;                    // quarters of the slot
+            const int need = (ts1_smem_bytes(ts1_ncol_class(d.n), d.h, esz) + per - 1) / per;
+            quarter = std::max(quarter, (need + 15) / 16 * 16);
+            b->max_cp = std::max<int64_t>(b->max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
+            ++at;
+        }
+        ph.end[k] = at;
     }
-    for (int k = 0; k < 9; ++k) {
-        std::stable_sort(cls[k].begin(), cls[k].end(), [](const Ts1Desc& x, const Ts1Desc& y) {
-            return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
-        });
-        b->ts1[k].count = static_cast<int>(cls[k].size());
-        if (!cls[k].empty() && upload(&b->ts1[k].d, cls[k]) != cudaSuccess) return TQR_ERR_NOMEM;
-    }
-    b->n_fused = static_cast<int>(fused.size());
+    ph.quarter_bytes = quarter;
+    b->ts1_ph = ph;
+    b->n_fused = static_cast<int>(q.size());
+    if (!q.empty() && upload(&b->ts1, q) != cudaSuccess) return TQR_ERR_NOMEM;
     return TQR_OK;
 }
 
@@ -1128,7 +1141,7 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
             cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMemset(b->tau_ge, 0, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
             cudaMemset(b->tau_el, 0, std::max<int64_t>(1, tau_off) * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&b->status, 4 * sizeof(int32_t)) != cudaSuccess ||
             (b->has_exec && alloc_state(b->st, b->dg.d.ntasks, b->status) != cudaSuccess))
             return TQR_ERR_NOMEM;
         if (build_ts1(b, fused) != TQR_OK) return TQR_ERR_NOMEM;
@@ -1190,7 +1203,7 @@ int tqr_factor_batched_f32(int count, float* const* A, const int64_t* m, const i
             cudaMalloc(&b->tau_el, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
             cudaMemset(b->tau_ge, 0, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
             cudaMemset(b->tau_el, 0, std::max<int64_t>(1, tau_off) * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&b->status, sizeof(int32_t)) != cudaSuccess)
+            cudaMalloc(&b->status, 4 * sizeof(int32_t)) != cudaSuccess)
             return TQR_ERR_NOMEM;
         if (build_ts1(b, fused) != TQR_OK) return TQR_ERR_NOMEM;
         b->stream = static_cast<cudaStream_t>(stream);

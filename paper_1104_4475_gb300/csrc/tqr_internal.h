@@ -174,8 +174,19 @@ struct Ts1Desc {
 int ts1_ncol_class(int64_t n);
 int ts1_smem_bytes(int ncol_class, int h, int elem_size);
 bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size);
-cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int h, bool f32, void* tau_ge,
-                       void* tau_el, int32_t* status, cudaStream_t s);
+// Threads a matrix of the class runs with: 256, 512 or 1024.
+int ts1_threads(int ncol_class, int h, int elem_size);
+// The persistent launch's queues: descriptors [begin[k], end[k]) run on slots
+// of 1024 >> k threads (begin[0] = 0, end[k] = begin[k + 1], end[2] = count);
+// a slot of 1024 >> k threads has (4 >> k) * quarter_bytes of shared memory.
+struct Ts1Phases {
+    int32_t begin[3], end[3];
+    int32_t quarter_bytes;
+};
+// One launch for every one-tile-column matrix of a batch; ctr: three counters
+// that must be zero when the kernel starts.
+cudaError_t launch_ts1_all(const Ts1Desc* d, const Ts1Phases& ph, bool f32, void* tau_ge, void* tau_el,
+                           int32_t* status, int32_t* ctr, cudaStream_t s);
 // T factors of the listed panel tasks (kind, i, k triplets on the device).
 cudaError_t launch_form_t(const ExecParams& P, const int32_t* panels, int npanels,
                           double* T_ge, double* T_el, cudaStream_t s);

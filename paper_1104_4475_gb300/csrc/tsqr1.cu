@@ -26,9 +26,16 @@
 // it, so the same code updates R's row j; for TSQRT R's row j lives in shared
 // memory (packed) and lane 0 of each column adds and updates it.  The group of
 // column j+1 forms reflector j+1 right after its own update and publishes u
-// in the second of two buffers: one block barrier per reflector.  Tiles move
+// in the second of two buffers: one barrier per reflector.  Tiles move
 // between global memory and registers through a shared staging tile
 // (coalesced global loads and stores).
+//
+// The whole batch is one persistent launch (ts1_all_kernel): one CTA of 1024
+// threads per SM, whose threads form slots of 1024, 512 or 256 threads (the
+// thread count of a matrix's class).  Each slot pops matrices, largest first,
+// from a queue per thread count and synchronises on a named barrier of its
+// own, so a CTA runs up to four matrices at once and the SMs balance
+// themselves without one launch per class.
 #include "tqr_internal.h"
 #include "reflector.cuh"
 #include "../../include/tqr.h"
@@ -50,6 +57,8 @@ __device__ __forceinline__ Real group_sum(Real x, int G, unsigned gmask) {
 }
 
 __device__ __forceinline__ int packed(int j, int c) { return c * (c + 1) / 2 + j; }
+
+__device__ __forceinline__ int ts1_ncol_class_dev(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
 
 // Shared-memory geometry of one (Real, NCOL, RPT) instantiation.
 template <typename Real, int NCOL, int RPT, int NT>
@@ -159,21 +168,25 @@ __device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, 
     }
 }
 
+// Named barrier `id` (1..4) over the nt threads of one slot.
+__device__ __forceinline__ void slot_sync(int id, int nt) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory");
+}
+
+// Factors one matrix with the NT threads t = 0..NT-1 of a slot; sm is the
+// slot's shared memory (Ts1Geom::ELEMS elements), s_tau two scalars of it,
+// bar its named barrier.
 template <typename Real, int NCOL, int RPT, int NT>
-__global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ descs, Real* tau_ge, Real* tau_el,
-                                                  int32_t* status) {
+__device__ __forceinline__ void ts1_body(const Ts1Desc& d, Real* sm, Real* s_tau, Real* tau_ge, Real* tau_el,
+                                         int32_t* status, int t, int bar) {
     using Geo = Ts1Geom<Real, NCOL, RPT, NT>;
     constexpr int G = Geo::G, H = Geo::H, LD = Geo::LD, UCH = Geo::UCH, ULEN = Geo::ULEN;
-    extern __shared__ __align__(16) unsigned char ts1_raw[];
-    __shared__ Real s_tau[2];
-    Real* Ub = reinterpret_cast<Real*>(ts1_raw);   // 2 published vectors (16-byte aligned chunks)
+    Real* Ub = sm;                                 // 2 published vectors (16-byte aligned chunks)
     Real* T = Ub + 2 * ULEN;                       // staging tile: H x LD, row-major
     Real* R = T + H * LD;                          // packed upper triangle of R
-    const Ts1Desc d = descs[blockIdx.x];
     const int n = d.n;
     const int64_t m = d.m;
     Real* A = static_cast<Real*>(d.A);
-    const int t = threadIdx.x;
     const int c = t / G, g = t % G;
     const int lane = t & 31;
     const int leader = lane & ~(G - 1);
@@ -187,17 +200,17 @@ __global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ des
         const int64_t row0 = static_cast<int64_t>(tile) * H;
         const int rows = static_cast<int>(m - row0 < H ? m - row0 : H);
         Real* tau_out = (ge ? tau_ge : tau_el) + d.tau_off + static_cast<int64_t>(tile) * H;
-        __syncthreads();
+        slot_sync(bar, NT);
         for (int e = t; e < H * n; e += NT) {
             const int r = e % H, cc = e / H;
             T[r * LD + cc] = r < rows ? A[row0 + r + static_cast<int64_t>(cc) * m] : Real(0);
         }
         for (int j = n + t; j < H; j += NT) tau_out[j] = Real(0);   // padded columns
-        __syncthreads();
+        slot_sync(bar, NT);
 #pragma unroll
         for (int k = 0; k < RPT; ++k) x[k] = c < n ? T[(r0 + k) * LD + c] : Real(0);
         if (c == 0) ts1_form<Real, RPT>(ge, 0, r0, g, G, gmask, x, Ub + g * UCH, R, &s_tau[0], &tau_out[0], status);
-        __syncthreads();
+        slot_sync(bar, NT);
 
         for (int j = 0; j < n - 1; ++j) {
             if (c > j && c < n) {
@@ -213,14 +226,14 @@ __global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ des
                     ts1_form<Real, RPT>(ge, j + 1, r0, g, G, gmask, x, Ub + ((j + 1) & 1) * ULEN + g * UCH, R,
                                         &s_tau[(j + 1) & 1], &tau_out[j + 1], status);
             }
-            __syncthreads();
+            slot_sync(bar, NT);
         }
 
         if (c < n) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) T[(r0 + k) * LD + c] = x[k];
         }
-        __syncthreads();
+        slot_sync(bar, NT);
         if (ge) {                                  // R = upper triangle of the factored first tile
             for (int e = t; e < n * (n + 1) / 2; e += NT) {
                 int cc = 0;
@@ -234,7 +247,7 @@ __global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ des
             A[row0 + r + static_cast<int64_t>(cc) * m] = T[r * LD + cc];
         }
     }
-    __syncthreads();
+    slot_sync(bar, NT);
     if (p > 1) {                                   // final R over the first tile's upper triangle
         for (int e = t; e < n * (n + 1) / 2; e += NT) {
             int cc = 0;
@@ -245,54 +258,85 @@ __global__ void __launch_bounds__(NT) ts1_kernel(const Ts1Desc* __restrict__ des
     }
 }
 
-template <typename Real, int NCOL, int NT, int H>
-cudaError_t launch_one(const Ts1Desc* d, int count, void* tau_ge, void* tau_el, int32_t* status, cudaStream_t s) {
-    constexpr int RPT = H * NCOL / NT;
-    const int smem = Ts1Geom<Real, NCOL, RPT, NT>::ELEMS * static_cast<int>(sizeof(Real));
-    auto* k = ts1_kernel<Real, NCOL, RPT, NT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k<<<count, NT, smem, s>>>(d, static_cast<Real*>(tau_ge), static_cast<Real*>(tau_el), status);
-    return cudaGetLastError();
-}
-
-// Threads per CTA: enough that a thread holds at most 16 FP32 / 8 FP64 rows of
-// its column (RPT = nb * NCOL / NT), so that the reflector chain of one matrix
-// has many warps to hide its latency; at least 256 (FP32) / 512 (FP64), at
-// most 1024.
+// Threads per matrix: enough that a thread holds at most 16 FP32 / 8 FP64 rows
+// of its column (RPT = nb * NCOL / NT), so that the reflector chain of one
+// matrix has many warps to hide its latency; at least 256 (FP32) / 512 (FP64),
+// at most 1024.  Always a power of two: 256, 512 or 1024.
 constexpr int threads_for(int esz, int ncol, int h) {
     const int want = h * ncol / (esz == 4 ? 16 : 8);
     const int lo = esz == 4 ? 256 : 512;
     return want < lo ? lo : (want > 1024 ? 1024 : want);
 }
 
-// Instantiated (column class, tile height) pairs.
-template <typename Real, int NCOL, int H>
-cudaError_t launch_nt(const Ts1Desc* d, int count, void* tg, void* te, int32_t* st, cudaStream_t s) {
-    return launch_one<Real, NCOL, threads_for(sizeof(Real), NCOL, H), H>(d, count, tg, te, st, s);
-}
-
-template <typename Real>
-cudaError_t launch_typed(const Ts1Desc* d, int count, int ncol, int h, void* tg, void* te, int32_t* st,
-                         cudaStream_t s) {
-    switch (ncol * 1000 + h) {
-        case 32064: return launch_nt<Real, 32, 64>(d, count, tg, te, st, s);
-        case 32128: return launch_nt<Real, 32, 128>(d, count, tg, te, st, s);
-        case 32256: return launch_nt<Real, 32, 256>(d, count, tg, te, st, s);
-        case 64064: return launch_nt<Real, 64, 64>(d, count, tg, te, st, s);
-        case 64128: return launch_nt<Real, 64, 128>(d, count, tg, te, st, s);
-        case 64256: return launch_nt<Real, 64, 256>(d, count, tg, te, st, s);
-        case 128128: return launch_nt<Real, 128, 128>(d, count, tg, te, st, s);
-        case 128256:
-            if constexpr (sizeof(Real) == 4) return launch_nt<Real, 128, 256>(d, count, tg, te, st, s);
-            return cudaErrorInvalidValue;                        // 32 FP64 rows per thread at 1024 threads
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 int geom_elems(int ncol, int h, int esz) {
     const int G = threads_for(esz, ncol, h) / ncol, rpt = h / G, vpad = 16 / esz;
     return 2 * G * (rpt + vpad) + h * (ncol + 1) + ncol * (ncol + 1) / 2;
+}
+
+// Runs matrices of one class (threads_for == NT) with the slot's threads.
+template <typename Real, int NCOL, int H, int NT>
+__device__ __forceinline__ void ts1_class(const Ts1Desc& d, Real* sm, Real* s_tau, Real* tg, Real* te,
+                                          int32_t* status, int t, int bar) {
+    if constexpr (threads_for(sizeof(Real), NCOL, H) == NT && !(sizeof(Real) == 8 && NCOL == 128 && H == 256))
+        ts1_body<Real, NCOL, H * NCOL / NT, NT>(d, sm, s_tau, tg, te, status, t, bar);
+}
+
+// One phase of the persistent kernel: slots of NT threads pop matrices of
+// their phase (descriptors ph.begin..ph.end, largest first) until none is
+// left.  Slot s covers threads [s NT, (s+1) NT) and shared-memory quarters
+// [s NT/256, (s+1) NT/256): a slot of a later phase never shares memory or a
+// barrier with a slot of an earlier phase that may still run.
+template <typename Real, int NT>
+__device__ __forceinline__ void ts1_phase(const Ts1Desc* __restrict__ descs, int begin, int end, int32_t* ctr,
+                                          unsigned char* raw, int quarter_bytes, Real* tg, Real* te,
+                                          int32_t* status, int* s_next, Real (*s_tau)[2]) {
+    // s_next: this phase's own four words, so that a thread still reading the
+    // previous phase's last (failed) pop never sees this phase's values.
+    const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
+    const int q0 = slot * (NT / 256);              // first quarter of the slot
+    const int bar = 1 + q0;
+    Real* sm = reinterpret_cast<Real*>(raw + static_cast<size_t>(q0) * quarter_bytes);
+    for (;;) {
+        if (t == 0) s_next[q0] = begin + atomicAdd(ctr, 1);
+        slot_sync(bar, NT);
+        const int k = s_next[q0];
+        if (k >= end) break;                       // uniform over the slot
+        const Ts1Desc d = descs[k];
+        switch (ts1_ncol_class_dev(d.n) * 1000 + d.h) {
+            case 32064: ts1_class<Real, 32, 64, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 32128: ts1_class<Real, 32, 128, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 32256: ts1_class<Real, 32, 256, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 64064: ts1_class<Real, 64, 64, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 64128: ts1_class<Real, 64, 128, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 64256: ts1_class<Real, 64, 256, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 128128: ts1_class<Real, 128, 128, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            case 128256: ts1_class<Real, 128, 256, NT>(d, sm, s_tau[q0], tg, te, status, t, bar); break;
+            default: break;                        // the host sorts only supported classes into a phase
+        }
+        slot_sync(bar, NT);                        // every thread has read s_next before it is rewritten
+    }
+}
+
+// The whole one-tile-column batch in one persistent launch: one CTA of 1024
+// threads per SM runs the 1024-thread matrices, then two slots of 512, then
+// four slots of 256, each slot popping the next matrix from its phase's
+// queue (atomic counter ctr[phase], zeroed before the launch).
+template <typename Real>
+__global__ void __launch_bounds__(1024, 1) ts1_all_kernel(const Ts1Desc* __restrict__ descs, Ts1Phases ph,
+                                                           Real* tau_ge, Real* tau_el, int32_t* status,
+                                                           int32_t* ctr) {
+    extern __shared__ __align__(16) unsigned char ts1_raw[];
+    __shared__ int s_next[3][4];
+    __shared__ Real s_tau[4][2];
+    if (ph.begin[0] < ph.end[0])
+        ts1_phase<Real, 1024>(descs, ph.begin[0], ph.end[0], ctr + 0, ts1_raw, ph.quarter_bytes, tau_ge, tau_el,
+                              status, s_next[0], s_tau);
+    if (ph.begin[1] < ph.end[1])
+        ts1_phase<Real, 512>(descs, ph.begin[1], ph.end[1], ctr + 1, ts1_raw, ph.quarter_bytes, tau_ge, tau_el,
+                             status, s_next[1], s_tau);
+    if (ph.begin[2] < ph.end[2])
+        ts1_phase<Real, 256>(descs, ph.begin[2], ph.end[2], ctr + 2, ts1_raw, ph.quarter_bytes, tau_ge, tau_el,
+                             status, s_next[2], s_tau);
 }
 
 }  // namespace
@@ -311,14 +355,31 @@ bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 227 * 1024;
-    return ts1_smem_bytes(cls, nb, elem_size) <= optin;
+    return ts1_smem_bytes(cls, nb, elem_size) + 256 <= optin;   // + the kernel's static words and rounding
 }
 
-cudaError_t launch_ts1(const Ts1Desc* d, int count, int ncol_class, int h, bool f32, void* tau_ge, void* tau_el,
-                       int32_t* status, cudaStream_t s) {
+int ts1_threads(int ncol_class, int h, int elem_size) { return threads_for(elem_size, ncol_class, h); }
+
+cudaError_t launch_ts1_all(const Ts1Desc* d, const Ts1Phases& ph, bool f32, void* tau_ge, void* tau_el,
+                           int32_t* status, int32_t* ctr, cudaStream_t s) {
+    const int count = ph.end[2];
     if (count == 0) return cudaSuccess;
-    return f32 ? launch_typed<float>(d, count, ncol_class, h, tau_ge, tau_el, status, s)
-               : launch_typed<double>(d, count, ncol_class, h, tau_ge, tau_el, status, s);
+    const int smem = 4 * ph.quarter_bytes;
+    const int nsm = device_sm_count();
+    if (nsm < 1) return cudaErrorInvalidDevice;
+    const int grid = count < nsm ? count : nsm;
+    if (f32) {
+        auto* k = ts1_all_kernel<float>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 1024, smem, s>>>(d, ph, static_cast<float*>(tau_ge), static_cast<float*>(tau_el), status, ctr);
+    } else {
+        auto* k = ts1_all_kernel<double>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 1024, smem, s>>>(d, ph, static_cast<double*>(tau_ge), static_cast<double*>(tau_el), status, ctr);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace tqr

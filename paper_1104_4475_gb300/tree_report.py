@@ -56,7 +56,7 @@ def sweep_report(line, m, nb, n_sm, peak_gflops):
     return out
 
 
-def markdown(rep):
+def markdown(rep, n_sm=152):
     """Markdown tables: measured / predicted rate, overhead vs Greedy, and (when
     traced) measured critical path vs traced makespan."""
     qs = sorted({q for rows in rep.values() for q in rows})
@@ -72,6 +72,15 @@ def markdown(rep):
         b.append("| %s | " % tree + " | ".join(
             "%.2f / %.2f" % (rows[q]["cp_over_greedy"], rows[q]["time_over_greedy"])
             if q in rows and rows[q]["cp_over_greedy"] is not None else "" for q in qs) + " |")
+    d = ["", "Unit-weight critical path (units of nb^3/3; PlasmaTree BS after the slash) and the work "
+         "bound T/P:", "", head, sep]
+    for tree, rows in rep.items():
+        d.append("| %s | " % tree + " | ".join(
+            ("%d/%d" % (rows[q]["cp"], rows[q]["BS"]) if rows[q].get("BS", 1) not in (None, 1) or "Plasma" in tree
+             else "%d" % rows[q]["cp"]) + (" (cp)" if rows[q]["bound"] == "cp" else "")
+            if q in rows else "" for q in qs) + " |")
+    any_rows = next(iter(rep.values()))
+    d.append("| T/P | " + " | ".join("%.0f" % (any_rows[q]["T"] / n_sm) if q in any_rows else "" for q in qs) + " |")
     c = []
     if any(r["measured_cp_ms"] is not None for rows in rep.values() for r in rows.values()):
         c = ["", "Measured critical path / traced makespan, ms (bench --trace-cp):", "", head, sep]
@@ -79,7 +88,7 @@ def markdown(rep):
             c.append("| %s | " % tree + " | ".join(
                 "%.1f / %.1f" % (rows[q]["measured_cp_ms"], rows[q]["traced_makespan_ms"])
                 if q in rows and rows[q]["measured_cp_ms"] is not None else "" for q in qs) + " |")
-    return "\n".join(a + b + c)
+    return "\n".join(a + d + b + c)
 
 
 def main(argv=None):
@@ -88,12 +97,16 @@ def main(argv=None):
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--nb", type=int, default=256)
     ap.add_argument("--sms", type=int, default=152)
-    ap.add_argument("--peak", type=float, default=152 * 4 * 2.07, help="FP64 GFLOP/s of the whole GPU")
+    ap.add_argument("--peak", type=float, default=None,
+                    help="FP64 GFLOP/s of the whole GPU (default: the DFMA peak the bench line measured)")
     a = ap.parse_args(argv)
     with open(a.path) as fh:
         lines = [ln for ln in fh.read().splitlines() if ln.strip().startswith("{")]
     line = json.loads(lines[-1])
-    print(markdown(sweep_report(line, a.m, a.nb, a.sms, a.peak)))
+    peak = a.peak
+    if peak is None:
+        peak = 1e3 * line["measured_peaks"]["dfma_tflops"] if "measured_peaks" in line else 152 * 4 * 2.07
+    print(markdown(sweep_report(line, a.m, a.nb, a.sms, peak), a.sms))
     return 0
 
 

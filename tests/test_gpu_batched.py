@@ -220,3 +220,52 @@ def test_one_column_degenerate_inputs():
     tg, te = tqr.tqr_batch_tau(b, 0, 400, 96, 128, f32=True)
     assert not tg.any() and not te.any()
     b.free()
+
+
+def one_column_shapes(count, seed, f32):
+    """Shapes over every (column class, tile height) pair the one-column
+    kernel takes, so a batch fills all of its thread-count queues."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        nb = int(rng.choice([64, 128, 256]))
+        n = int(rng.integers(1, min(nb, 128) + 1))
+        if not f32 and n > 64 and nb == 256:
+            continue                                   # FP64 class 128 needs nb = 128
+        m = int(rng.integers(n, 3000))
+        out.append((m, n, nb))
+    return out
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_persistent_queue_equals_one_matrix_batches(f32):
+    """600 matrices of every class in one persistent launch (slots of 1024,
+    512 and 256 threads popping from their queues) give bit for bit what
+    each matrix gives alone in a batch of one: no slot, queue position or
+    phase change alters a result.  A sample is also checked against the
+    oracle."""
+    shapes = one_column_shapes(600, 17 + f32, f32)
+    dt = torch.float32 if f32 else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(3)
+    src = [torch.randn(n, m, generator=g, dtype=dt, device="cuda").t() for m, n, _ in shapes]
+    nbs = [nb for _, _, nb in shapes]
+    work = [s.t().clone().t() for s in src]                # copies (contiguous() would return s itself)
+    b = tqr.tqr_factor_batched_f32(work, nbs) if f32 else tqr.tqr_factor_batched(work, nbs, 8, tqr.FLAT_TS, 1)
+    assert tqr.tqr_batch_sync(b) == 0 and b.info()["n_fused"] == len(shapes)
+    b.free()
+    for c in range(len(shapes)):
+        one = [src[c].t().clone().t()]
+        b1 = (tqr.tqr_factor_batched_f32(one, nbs[c]) if f32
+              else tqr.tqr_factor_batched(one, nbs[c], 8, tqr.FLAT_TS, 1))
+        assert tqr.tqr_batch_sync(b1) == 0
+        assert one[0].data_ptr() != work[c].data_ptr() and not torch.equal(one[0], src[c])
+        assert torch.equal(one[0], work[c]), (shapes[c], c)
+        b1.free()
+    for c in range(0, len(shapes), 75):
+        m, n, nb = shapes[c]
+        A = src[c].double().cpu().numpy()
+        F = otq.factor(A, nb, 8, O_FLAT_TS)
+        u = U32 if f32 else U
+        tol = max(1e-13, 8 * np.linalg.cond(A) * m * u)
+        got = work[c].double().cpu().numpy()
+        assert np.abs(got - F.A).max() / np.abs(F.r()).max() <= tol, shapes[c]

@@ -112,16 +112,17 @@ def test_training_fits_smooth_function(tqr):
 
 
 def test_trained_model_gains_over_fixed_configuration(tqr):
-    """Trained on executor timings of 100 shapes (GB300, 18 configurations
-    each), the network's pick on 200 other shapes (timed the same way) is
-    within 2 % of the exhaustive best on average, and better than both the
-    fixed default (Greedy, nb 256) and the smallest-critical-path rule."""
+    """Trained on executor timings of 100 shapes (GB300, 30 configurations
+    each: nb, ib, tree, BS and precision all vary), the network's pick on 200
+    other shapes (timed the same way) is within 2 % of the exhaustive best on
+    average, and better than both the fixed default (Greedy, nb 256) and the
+    smallest-critical-path rule, in FP64 and split-TF32."""
     import os
     from paper_1104_4475_gb300 import costmodel
     data = os.path.join(os.path.dirname(costmodel.__file__), "data")
     train = costmodel.load_records(os.path.join(data, "costmodel_timings_gb300.csv"))
     test = costmodel.disjoint(train, costmodel.load_records(os.path.join(data, "costmodel_heldout_gb300.csv")))
-    assert len(costmodel.by_shape(test)) >= 195
+    assert len(costmodel.by_shape(test)) == 200
     X, y = costmodel.design(train)
     model, losses = costmodel.train(X, y, steps=3000)
     assert losses[-1][1] < 0.01 * losses[0][1]
@@ -129,7 +130,10 @@ def test_trained_model_gains_over_fixed_configuration(tqr):
     assert s["model_over_best"] <= 1.02
     assert s["model_over_best"] < s["default_over_best"]
     assert s["model_over_best"] <= s["min_cp_over_best"]
-    assert s["model_worst"] <= 1.10
+    assert s["model_worst"] <= 1.12
+    lp = costmodel.summarize(costmodel.evaluate(model, test, 1))
+    assert lp["shapes"] == 200 and lp["model_over_best"] <= 1.02
+    assert lp["model_over_best"] < lp["default_over_best"] and lp["model_over_best"] <= lp["min_cp_over_best"]
     m, n = test[0]["m"], test[0]["n"]
     c = costmodel.pick(model, m, n)
     assert c in costmodel.configs_for(m) and c[4] == 0

@@ -82,3 +82,23 @@ def test_full_size_bench_configuration(q):
     assert orth <= 1e-13, orth
     assert abs(np.linalg.norm(tqr.to_numpy(bt)) - np.linalg.norm(b)) <= 1e-13 * np.linalg.norm(b)
     f.free()
+
+
+def test_full_q8_factorization_against_oracle():
+    """The complete q = 8 sweep point (16384 x 2048, the benchmark's tree and
+    launch configuration) element by element against the oracle's
+    factorization of the same matrix: R and every reflector, about a minute
+    of oracle time."""
+    q = 8
+    name, BS = bench.SWEEP_TREES[q]
+    tree = tqr.TREES[name]
+    A = workloads.sweep_config(q)
+    At = tqr.colmajor(A)
+    f = tqr.tqr_factor(At, NB, IB, tree, BS)
+    assert tqr.tqr_sync(f) == 0
+    got = tqr.to_numpy(At)
+    f.free()
+    F = otq.factor(A, NB, IB, tree, BS)
+    tol = max(1e-13, 8 * np.linalg.cond(A) * M * U)
+    err = np.abs(got - F.A).max() / np.abs(F.r()).max()
+    assert err <= tol, (err, tol)
