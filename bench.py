@@ -53,12 +53,14 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12
 CPU_SAMPLE_QS = (1, 2, 4)
 REF_SAMPLE_QS = (1, 2)
 # DRAM bytes per algorithmic flop of the FP64 executor: dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of the q = 8 Greedy launch of this
-# sweep (2.727 + 2.635 GB for 1.3174e11 flop).  The traffic comes from
-# re-staging reflector blocks and strips per update task, so it grows with the
-# number of strip tasks, i.e. in proportion to the flops at fixed nb and ib;
-# the sweep's per-step traffic is this ratio times the sweep's flops.
-TRAFFIC_BYTES_PER_FLOP = 5.3618e9 / 1.3174e11
+# dram__bytes_write.sum of one ncu capture of the q = 16 PlasmaTree-TS(8)
+# launch of this sweep (9.244 + 8.424 GB for 5.039e11 flop; the q = 8 Greedy
+# launch gave 5.362 GB for 1.3174e11, 0.0407 bytes per flop).  The traffic
+# comes from re-staging reflector blocks and strips per update task, so it
+# grows with the number of strip tasks, i.e. in proportion to the flops at
+# fixed nb and ib; the sweep's per-step traffic is this ratio times the
+# sweep's flops.
+TRAFFIC_BYTES_PER_FLOP = 17.6678e9 / 5.0394e11
 
 
 def flops(m, n):
@@ -446,7 +448,7 @@ def gpu_main(args):
                          "traffic": args.traffic if args.traffic is not None
                          else TRAFFIC_BYTES_PER_FLOP * workload_flops(),
                          "traffic_unit": "bytes per step (7 launches), estimated from the DRAM bytes per "
-                                         "flop of an ncu capture of the Greedy q = 8 launch",
+                                         "flop of an ncu capture of the q = 16 PlasmaTree-TS(8) launch",
                          "algorithmic_bytes": sum(16.0 * M * NB * q for q in QS),
                          "kernel": "exec_kernel<4> (persistent executor; events around each tqr_factor)",
                          "peak_source": "measured in this run: FP64 FMA probe (DFMA; the executor's "
