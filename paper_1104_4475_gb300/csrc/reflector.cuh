@@ -17,7 +17,7 @@
 // 2^-44 after one step, below the FP64 rounding level after two), so the
 // results are within a few ulp of the correctly rounded ones.  Where s lies
 // outside the range in which the FP32 seeds are accurate the IEEE sqrt and
-// divisions are used.  FP32 reflectors use the IEEE operations directly.
+// divisions are used.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,12 +51,27 @@ __device__ __forceinline__ void reflector_scalars(double alpha, double sig, doub
     }
 }
 
+// FP32: r = rsqrtf(s) (within 2 ulp) gives sqrt(s) = s r and 1/beta = -sign(alpha) r,
+// and scale is the correctly rounded reciprocal; no IEEE square root or
+// division sequence on the reflector's chain.  Outside (1e-30, 1e30) the IEEE
+// operations are used.
 __device__ __forceinline__ void reflector_scalars(float alpha, float sig, float* beta, float* tau, float* scale) {
-    const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-    const float b = alpha >= 0.0f ? -nrm : nrm;
-    *beta = b;
-    *tau = (b - alpha) / b;
-    *scale = 1.0f / (alpha - b);
+    const float s = fmaf(alpha, alpha, sig);
+    if (s > 1e-30f && s < 1e30f) {
+        const float r = rsqrtf(s);
+        const float nrm = s * r;
+        const float b = alpha >= 0.0f ? -nrm : nrm;
+        const float rb = alpha >= 0.0f ? -r : r;                  // 1 / beta
+        *beta = b;
+        *tau = (b - alpha) * rb;
+        *scale = __frcp_rn(alpha - b);
+    } else {
+        const float nrm = sqrtf(s);
+        const float b = alpha >= 0.0f ? -nrm : nrm;
+        *beta = b;
+        *tau = (b - alpha) / b;
+        *scale = 1.0f / (alpha - b);
+    }
 }
 
 }  // namespace tqr

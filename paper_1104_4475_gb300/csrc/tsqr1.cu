@@ -139,7 +139,8 @@ __device__ __forceinline__ void ts1_form(bool ge, int jn, int r0, int g, int G, 
         if (ge && row == jn) a = x[k];
     }
     sig = group_sum(sig, G, gmask);
-    if (ge) a = group_sum(a, G, gmask);
+    // GE: alpha (row jn) lives in lane jn / RPT of the group; one shuffle.
+    if (ge) a = __shfl_sync(gmask, a, ((threadIdx.x & 31) & ~(G - 1)) + jn / RPT);
     Real tau = Real(0), scale = Real(0), beta = a;
     if (sig != Real(0) || !isfinite(sig)) reflector_scalars(a, sig, &beta, &tau, &scale);
     if (g == 0) {
