@@ -361,6 +361,12 @@ __device__ void factor_block(const Smem& S, int nb, int j0, int ib, int32_t* sta
 
 template <int MODE>
 __device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch);
+// In low precision, panel_factor keeps the block's FP32 reflectors (unit and
+// zero entries written out, leading dimension nb + 1) in the strip buffer,
+// after form_t_block's Gram and T.
+__device__ __forceinline__ float* lp_block_v32(double* scratch, int ib) {
+    return reinterpret_cast<float*>(scratch + 2 * ib * ib);
+}
 template <int G, int MODE, int PREC>
 __device__ void panel_lp_trailing(const ExecParams& P, int i, int k, const View& top, const View& bot, int j0,
                                   int c_lo, int c_hi, double* smem);
@@ -422,6 +428,7 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
         // T_b in FP64 (Cs is free here), V_b and T_b stored as FP32.
         float* Tdst = ((MODE == GE) ? P.T_ge : P.T_el) + tile * ib * nb;
         float* Vdst = ((MODE == GE) ? P.V_ge : P.V_el) + tile * nb * nb;
+        float* V32 = lp_block_v32(S.Cs, ib);                   // the same FP32 block, for T's Gram
         for (int idx = threadIdx.x; idx < nb * ib; idx += kThreads) {
             const int r = idx % nb, jj = idx / nb, j = j0 + jj;
             float v;
@@ -429,7 +436,9 @@ __device__ void panel_factor(const ExecParams& P, int i, int piv, int k, int j0,
             else if (MODE == TT) v = (r <= j) ? static_cast<float>(S.Vs[r + jj * S.ldv]) : 0.0f;
             else v = static_cast<float>(S.Vs[r + jj * S.ldv]);
             Vdst[r + static_cast<int64_t>(j) * nb] = v;
+            V32[r + jj * (nb + 1)] = v;
         }
+        __syncthreads();
         form_t_block<MODE>(S, nb, j0, ib, Tdst + static_cast<int64_t>(j0) * ib, S.Cs);
     }
 }
@@ -650,27 +659,49 @@ __device__ void update_task_g(const ExecParams& P, const DevTask& T, const Smem&
 // accumulation).  Split-TF32 writes each operand x = hi + lo (hi = tf32(x),
 // lo = tf32(x - hi)) and sums hi*hi + hi*lo + lo*hi.  C stays in FP64.
 // ----------------------------------------------------------------------------
+// Dot product of two FP32 columns over rows [lo, hi), exact products
+// (a b = p + e by one FMA) summed with TwoSum's error terms carried along:
+// the result is the exact dot product to about 2^-48 relative (absent heavy
+// cancellation), from FP32 instructions only.
+__device__ __forceinline__ double dot_f32_compensated(const float* a, const float* b, int lo, int hi) {
+    // _rn intrinsics: no contraction into FMAs, which would break the error terms.
+    float s = 0.0f, err = 0.0f;
+    for (int x = lo; x < hi; ++x) {
+        const float p = __fmul_rn(a[x], b[x]);
+        const float pe = fmaf(a[x], b[x], -p);
+        const float t = __fadd_rn(s, p);
+        const float bv = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+        err = __fadd_rn(err, __fadd_rn(e, pe));
+        s = t;
+    }
+    return static_cast<double>(s) + static_cast<double>(err);
+}
+
 template <int MODE>
 __device__ void form_t_block(const Smem& S, int nb, int j0, int ib, float* Tout, double* scratch) {
     double* Gm = scratch;             // ib x ib Gram of the block's full reflector vectors
     double* Tb = scratch + ib * ib;   // ib x ib T
+    const float* V32 = lp_block_v32(scratch, ib);
+    const int ld32 = nb + 1;
     for (int idx = threadIdx.x; idx < ib * ib; idx += kThreads) {
-        const int r = idx % ib, c = idx / ib;
-        double s = 0.0;
-        if (r < c) {
-            const double* vr = S.Vs + r * S.ldv;
-            const double* vc = S.Vs + c * S.ldv;
-            const int jr = j0 + r, jc = j0 + c;
-            if (MODE == GE) {
-                s = vr[jc];                                  // tail of r . unit entry of c
-                for (int x = jc + 1; x < nb; ++x) s = fma(vr[x], vc[x], s);
-            } else {
-                const int hi = (MODE == TT) ? jr + 1 : nb;   // support of the tail of r
-                for (int x = 0; x < hi; ++x) s = fma(vr[x], vc[x], s);
-            }
-        }
-        Gm[idx] = s;
+        Gm[idx] = 0.0;
         Tb[idx] = 0.0;
+    }
+    __syncthreads();
+    // G[r, c] (r < c) of the FP32 vectors the updates apply, one pair per thread:
+    // pair p = c (c - 1) / 2 + r.  Rows: GE from c's unit entry on, TT up to
+    // r's last row, TS all.  FP32 arithmetic, compensated (the FP64 unit would
+    // take one 64-cycle slot per product).
+    const int npairs = ib * (ib - 1) / 2;
+    for (int p = threadIdx.x; p < npairs; p += kThreads) {
+        int c = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(p))) * 0.5f);
+        while (c * (c - 1) / 2 > p) --c;
+        while ((c + 1) * c / 2 <= p) ++c;
+        const int r = p - c * (c - 1) / 2;
+        const int lo = (MODE == GE) ? j0 + c : 0;
+        const int hi = (MODE == TT) ? j0 + r + 1 : nb;
+        Gm[r + c * ib] = dot_f32_compensated(V32 + r * ld32, V32 + c * ld32, lo, hi);
     }
     __syncthreads();
     for (int c = 0; c < ib; ++c) {
