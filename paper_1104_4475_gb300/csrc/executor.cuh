@@ -824,15 +824,22 @@ __device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane >> 2, tig = lane & 3;
     const int nmt1 = ib / 16;
-        // W = V_b^T C: warp w owns m-tile w % nmt1 and n-tiles (w / nmt1) + (8 / nmt1) t.
+        // W = V_b^T C: warp w owns m-tile w % nmt1 and n-tiles (w / nmt1) + (8 / nmt1) t
+        // (at most two in the layouts the low-precision path runs: 64-column strips, ib 16
+        // or 32).  Even and odd k-steps go to separate accumulators, summed at the end:
+        // twice the independent MMA chains.
         {
             const int m0 = (warp % nmt1) * 16;
-            constexpr int kMaxAcc = 8;
-            float acc[kMaxAcc][4];
+            constexpr int kMaxAcc = 2;
+            float acc[kMaxAcc][4], acc2[kMaxAcc][4];
             const int nstep = 8 / nmt1;
 #pragma unroll
-            for (int a = 0; a < kMaxAcc; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
+            for (int a = 0; a < kMaxAcc; ++a) {
+                acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.0f;
+                acc2[a][0] = acc2[a][1] = acc2[a][2] = acc2[a][3] = 0.0f;
+            }
             for (int k0 = rlo; k0 < rhi; k0 += 8) {
+                const bool odd = ((k0 - rlo) >> 3) & 1;
                 uint32_t ahi[4], alo[4];
                 split_t<PREC>(Vb[(k0 + tig) + (m0 + gid) * L.ldv], ahi[0], alo[0]);
                 split_t<PREC>(Vb[(k0 + tig) + (m0 + gid + 8) * L.ldv], ahi[1], alo[1]);
@@ -846,7 +853,8 @@ __device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib
                         uint32_t bh0, bl0, bh1, bl1;
                         split_t<PREC>(L.Cf[(k0 + tig) + (n0 + gid) * L.ldc], bh0, bl0);
                         split_t<PREC>(L.Cf[(k0 + tig + 4) + (n0 + gid) * L.ldc], bh1, bl1);
-                        mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
+                        if (odd) mma3<PREC>(acc2[a], ahi, alo, bh0, bh1, bl0, bl1);
+                        else mma3<PREC>(acc[a], ahi, alo, bh0, bh1, bl0, bl1);
                     }
                 }
             }
@@ -855,10 +863,10 @@ __device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib
                 const int nt = warp / nmt1 + a * nstep;
                 if (a * nstep < NNT && nt < NNT) {
                     const int n0 = nt * 8;
-                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig] = acc[a][0];
-                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig + 1] = acc[a][1];
-                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig] = acc[a][2];
-                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig + 1] = acc[a][3];
+                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig] = acc[a][0] + acc2[a][0];
+                    L.Wm[(m0 + gid) * L.ldw + n0 + 2 * tig + 1] = acc[a][1] + acc2[a][1];
+                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig] = acc[a][2] + acc2[a][2];
+                    L.Wm[(m0 + gid + 8) * L.ldw + n0 + 2 * tig + 1] = acc[a][3] + acc2[a][3];
                 }
             }
         }
@@ -880,27 +888,42 @@ __device__ void lp2_block(const Lp2& L, const float* Vb, const float* Tb, int ib
                 const int a = idx / W, n = idx % W;
                 L.Ctf[(j0 + a) + n * L.ldc] -= L.W2[a * L.ldw + n];
             }
-        // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...
+        // C[rlo:rhi, :] -= V_b W2: warp w owns m-tiles w, w+8, ...; four n-tiles at a
+        // time share each split A fragment and give four independent MMA chains.
+        constexpr int kNT = 4;
         for (int mt = (rlo / 16) + warp; mt < rhi / 16; mt += 8) {
             const int r0 = mt * 16;
-            for (int nt = 0; nt < NNT; ++nt) {
-                const int n0 = nt * 8;
-                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int nt0 = 0; nt0 < NNT; nt0 += kNT) {
+                float acc[kNT][4];
+#pragma unroll
+                for (int q = 0; q < kNT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0f;
                 for (int k0 = 0; k0 < ib; k0 += 8) {
                     uint32_t ahi[4], alo[4];
                     split_t<PREC>(Vb[(r0 + gid) + (k0 + tig) * L.ldv], ahi[0], alo[0]);
                     split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig) * L.ldv], ahi[1], alo[1]);
                     split_t<PREC>(Vb[(r0 + gid) + (k0 + tig + 4) * L.ldv], ahi[2], alo[2]);
                     split_t<PREC>(Vb[(r0 + gid + 8) + (k0 + tig + 4) * L.ldv], ahi[3], alo[3]);
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split_t<PREC>(L.W2[(k0 + tig) * L.ldw + n0 + gid], bh0, bl0);
-                    split_t<PREC>(L.W2[(k0 + tig + 4) * L.ldw + n0 + gid], bh1, bl1);
-                    mma3<PREC>(acc, ahi, alo, bh0, bh1, bl0, bl1);
+#pragma unroll
+                    for (int q = 0; q < kNT; ++q) {
+                        if (nt0 + q < NNT) {
+                            const int n0 = (nt0 + q) * 8;
+                            uint32_t bh0, bl0, bh1, bl1;
+                            split_t<PREC>(L.W2[(k0 + tig) * L.ldw + n0 + gid], bh0, bl0);
+                            split_t<PREC>(L.W2[(k0 + tig + 4) * L.ldw + n0 + gid], bh1, bl1);
+                            mma3<PREC>(acc[q], ahi, alo, bh0, bh1, bl0, bl1);
+                        }
+                    }
                 }
-                L.Cf[(r0 + gid) + (n0 + 2 * tig) * L.ldc] -= acc[0];
-                L.Cf[(r0 + gid) + (n0 + 2 * tig + 1) * L.ldc] -= acc[1];
-                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig) * L.ldc] -= acc[2];
-                L.Cf[(r0 + gid + 8) + (n0 + 2 * tig + 1) * L.ldc] -= acc[3];
+#pragma unroll
+                for (int q = 0; q < kNT; ++q) {
+                    if (nt0 + q < NNT) {
+                        const int n0 = (nt0 + q) * 8;
+                        L.Cf[(r0 + gid) + (n0 + 2 * tig) * L.ldc] -= acc[q][0];
+                        L.Cf[(r0 + gid) + (n0 + 2 * tig + 1) * L.ldc] -= acc[q][1];
+                        L.Cf[(r0 + gid + 8) + (n0 + 2 * tig) * L.ldc] -= acc[q][2];
+                        L.Cf[(r0 + gid + 8) + (n0 + 2 * tig + 1) * L.ldc] -= acc[q][3];
+                    }
+                }
             }
         }
 }
