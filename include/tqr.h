@@ -334,6 +334,17 @@ int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int6
  * batch's stream first. */
 int tqr_factor_batched_f32(int count, float* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,
                            void* stream, tqr_batch** out);
+/* Host only (no GPU, nothing allocated on a device): the queues of the batch's
+ * persistent one-tile-column launch for `count` matrices m[c] x n[c] with tile
+ * height nb[c] (FP32 when f32 is nonzero), each satisfying the one-tile-column
+ * conditions above.  order[i] receives the index of the i-th queued matrix
+ * (count entries); bounds[2k], bounds[2k+1] the begin and end of the queue of
+ * 1024 >> k threads (6 entries); *quarter_bytes the shared-memory quarter (a
+ * slot of t threads owns t/256 quarters).  Returns 0; -1 count, -2 m (or a
+ * null size array), -3 n, -5 a null output; TQR_ERR_UNSUPPORTED for a matrix
+ * the one-tile-column kernel does not take. */
+int tqr_ts1_plan(int count, const int64_t* m, const int64_t* n, const int32_t* nb, int f32, int32_t* order,
+                 int32_t* bounds, int32_t* quarter_bytes);
 int tqr_batch_tau(const tqr_batch* b, int c, void* tau_ge, void* tau_el);
 
 /* Waits for the batch's last launch; returns its device status. */

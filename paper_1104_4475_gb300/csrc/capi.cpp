@@ -1015,41 +1015,48 @@ static int launch_batch(tqr_batch* b) {
     return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }
 
-// Sorts the one-tile-column matrices of a batch into the persistent launch's
-// queues: by thread count (1024 first), then largest work first, so that the
-// slots finish together; sizes the shared-memory quarters (a slot of nt
-// threads owns nt/256 of them) and uploads the descriptors.
+// Plans the one-tile-column matrices of a batch into the persistent launch's
+// queues (plan_ts1) and uploads the descriptors.
 static int build_ts1(tqr_batch* b, const std::vector<Ts1Desc>& fused) {
-    const int esz = b->f32 ? 4 : 8;
-    auto phase = [esz](const Ts1Desc& d) {
-        const int nt = ts1_threads(ts1_ncol_class(d.n), d.h, esz);
-        return nt == 1024 ? 0 : (nt == 512 ? 1 : 2);
-    };
-    std::vector<Ts1Desc> q(fused);
-    std::stable_sort(q.begin(), q.end(), [&](const Ts1Desc& x, const Ts1Desc& y) {
-        const int px = phase(x), py = phase(y);
-        if (px != py) return px < py;
-        return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
-    });
-    Ts1Phases ph{};
-    int quarter = 16;
-    for (int k = 0, at = 0; k < 3; ++k) {
-        ph.begin[k] = at;
-        while (at < static_cast<int>(q.size()) && phase(q[at]) == k) {
-            const Ts1Desc& d = q[at];
-            const int per = (1024 >> k) / 256;                    // quarters of the slot
-            const int need = (ts1_smem_bytes(ts1_ncol_class(d.n), d.h, esz) + per - 1) / per;
-            quarter = std::max(quarter, (need + 15) / 16 * 16);
-            b->max_cp = std::max<int64_t>(b->max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
-            ++at;
-        }
-        ph.end[k] = at;
-    }
-    ph.quarter_bytes = quarter;
-    b->ts1_ph = ph;
+    std::vector<Ts1Desc> q;
+    plan_ts1(fused, b->f32 ? 4 : 8, &q, &b->ts1_ph, &b->max_cp);
     b->n_fused = static_cast<int>(q.size());
     if (!q.empty() && upload(&b->ts1, q) != cudaSuccess) return TQR_ERR_NOMEM;
     return TQR_OK;
+}
+
+int tqr_ts1_plan(int count, const int64_t* m, const int64_t* n, const int32_t* nb, int f32, int32_t* order,
+                 int32_t* bounds, int32_t* quarter_bytes) {
+    try {
+        if (count < 0 || count > (1 << 23)) return -1;
+        if (count > 0 && (!m || !n || !nb)) return -2;
+        if (!order || !bounds || !quarter_bytes) return -5;
+        const int esz = f32 ? 4 : 8;
+        std::vector<Ts1Desc> fused(count);
+        for (int c = 0; c < count; ++c) {
+            if (m[c] < 1) return -2;
+            if (n[c] < 1 || n[c] > m[c]) return -3;
+            if (!ts1_supported(m[c], n[c], nb[c], esz)) return TQR_ERR_UNSUPPORTED;
+            // the matrix's index in place of its pointer: this plan is never launched
+            fused[c] = Ts1Desc{reinterpret_cast<void*>(static_cast<intptr_t>(c) + 1), m[c], static_cast<int32_t>(n[c]),
+                               nb[c], 0};
+        }
+        std::vector<Ts1Desc> q;
+        Ts1Phases ph{};
+        int64_t cp = 0;
+        plan_ts1(fused, esz, &q, &ph, &cp);
+        for (int i = 0; i < count; ++i) order[i] = static_cast<int32_t>(reinterpret_cast<intptr_t>(q[i].A) - 1);
+        for (int k = 0; k < 3; ++k) {
+            bounds[2 * k] = ph.begin[k];
+            bounds[2 * k + 1] = ph.end[k];
+        }
+        *quarter_bytes = ph.quarter_bytes;
+        return TQR_OK;
+    } catch (const std::bad_alloc&) {
+        return TQR_ERR_NOMEM;
+    } catch (...) {
+        return TQR_ERR_INTERNAL;
+    }
 }
 
 int tqr_factor_batched(int count, double* const* A, const int64_t* m, const int64_t* n, const int32_t* nb,

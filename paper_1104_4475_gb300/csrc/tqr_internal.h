@@ -183,6 +183,12 @@ struct Ts1Phases {
     int32_t begin[3], end[3];
     int32_t quarter_bytes;
 };
+// The launch's queues (host only): the matrices sorted by thread count (1024
+// first), largest work m n^2 first within each, the phase bounds and the
+// shared-memory quarter (a multiple of 16 bytes that covers every slot's
+// need); *max_cp is raised to the longest chain (Proposition 2, q = 1).
+void plan_ts1(const std::vector<Ts1Desc>& fused, int elem_size, std::vector<Ts1Desc>* queue, Ts1Phases* ph,
+              int64_t* max_cp);
 // One launch for every one-tile-column matrix of a batch; ctr: three counters
 // that must be zero when the kernel starts.
 cudaError_t launch_ts1_all(const Ts1Desc* d, const Ts1Phases& ph, bool f32, void* tau_ge, void* tau_el,

@@ -42,7 +42,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 namespace tqr {
 
@@ -360,6 +362,37 @@ bool ts1_supported(int64_t m, int64_t n, int nb, int elem_size) {
 }
 
 int ts1_threads(int ncol_class, int h, int elem_size) { return threads_for(elem_size, ncol_class, h); }
+
+void plan_ts1(const std::vector<Ts1Desc>& fused, int elem_size, std::vector<Ts1Desc>* queue, Ts1Phases* ph,
+              int64_t* max_cp) {
+    auto phase = [elem_size](const Ts1Desc& d) {
+        const int nt = ts1_threads(ts1_ncol_class(d.n), d.h, elem_size);
+        return nt == 1024 ? 0 : (nt == 512 ? 1 : 2);
+    };
+    std::vector<Ts1Desc>& q = *queue;
+    q = fused;
+    std::stable_sort(q.begin(), q.end(), [&](const Ts1Desc& x, const Ts1Desc& y) {
+        const int px = phase(x), py = phase(y);
+        if (px != py) return px < py;
+        return static_cast<double>(x.m) * x.n * x.n > static_cast<double>(y.m) * y.n * y.n;
+    });
+    Ts1Phases out{};
+    int quarter = 16;
+    for (int k = 0, at = 0; k < 3; ++k) {
+        out.begin[k] = at;
+        while (at < static_cast<int>(q.size()) && phase(q[at]) == k) {
+            const Ts1Desc& d = q[at];
+            const int per = (1024 >> k) / 256;                    // quarters of the slot
+            const int need = (ts1_smem_bytes(ts1_ncol_class(d.n), d.h, elem_size) + per - 1) / per;
+            quarter = std::max(quarter, (need + 15) / 16 * 16);
+            *max_cp = std::max<int64_t>(*max_cp, 6 * ((d.m + d.h - 1) / d.h) - 2);   // Proposition 2, q = 1
+            ++at;
+        }
+        out.end[k] = at;
+    }
+    out.quarter_bytes = quarter;
+    *ph = out;
+}
 
 cudaError_t launch_ts1_all(const Ts1Desc* d, const Ts1Phases& ph, bool f32, void* tau_ge, void* tau_el,
                            int32_t* status, int32_t* ctr, cudaStream_t s) {

@@ -102,6 +102,7 @@ def lib():
                                    ctypes.POINTER(vp)],
             "tqr_batch_sync": [vp],
             "tqr_factor_batched_f32": [i32, ctypes.POINTER(vp), pi64, pi64, pi32, vp, ctypes.POINTER(vp)],
+            "tqr_ts1_plan": [i32, pi64, pi64, pi32, i32, pi32, pi32, pi32],
             "tqr_batch_tau": [vp, i32, vp, vp],
             "tqr_get_edges": [vp, pi32, pi32, i64, pi64],
             "tqr_poison_workspace": [vp],
@@ -611,6 +612,23 @@ def tqr_noalloc_graph(m, n, nb, ib, elims, ts=False, strip=64):
                                    tasks.ctypes.data_as(p32), tasks.shape[0], ctypes.byref(nt), src.ctypes.data_as(p32),
                                    dst.ctypes.data_as(p32), src.shape[0], ctypes.byref(ne)), "tqr_noalloc_graph")
     return tasks[: nt.value], np.stack([src[: ne.value], dst[: ne.value]], axis=1)
+
+
+def tqr_ts1_plan(m, n, nb, f32=False):
+    """The queues of the batch's persistent one-tile-column launch, planned on
+    the host (see tqr.h): (order, bounds (3, 2), quarter_bytes)."""
+    m = np.ascontiguousarray(m, dtype=np.int64)
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    nb = np.ascontiguousarray(np.broadcast_to(nb, m.shape), dtype=np.int32)
+    count = m.shape[0]
+    order = np.zeros(max(1, count), dtype=np.int32)
+    bounds = np.zeros(6, dtype=np.int32)
+    q = ctypes.c_int32(0)
+    p32, p64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    _check(lib().tqr_ts1_plan(count, m.ctypes.data_as(p64), n.ctypes.data_as(p64), nb.ctypes.data_as(p32),
+                              int(bool(f32)), order.ctypes.data_as(p32), bounds.ctypes.data_as(p32),
+                              ctypes.byref(q)), "tqr_ts1_plan")
+    return order[:count], bounds.reshape(3, 2), q.value
 
 
 PEAK_DFMA, PEAK_DMMA, PEAK_FFMA, PEAK_TF32 = range(4)
