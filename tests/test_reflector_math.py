@@ -77,3 +77,31 @@ def test_compensated_f32_dot_is_exact_to_fp64_level():
             worst_plain = max(worst_plain, abs(float(plain) - exact) / scale)
     assert worst <= 1e-12, worst
     assert worst_plain >= 1e-9                       # the compensation is doing the work
+
+
+def test_fp32_scalars_from_rsqrt_within_a_few_ulp():
+    """The one-column kernel's FP32 reflector scalars: r = rsqrtf(s) (2 ulp),
+    sqrt(s) = s r, 1/beta = -sign(alpha) r, scale = the correctly rounded
+    reciprocal of alpha - beta.  Emulated in float32 with r perturbed by 2 ulp:
+    beta, tau and scale stay within 8 ulp of the values computed in FP64."""
+    rng = np.random.default_rng(1)
+    f = np.float32
+    eps = float(np.finfo(np.float32).eps)
+    worst = 0.0
+    for _ in range(20000):
+        alpha = f(rng.standard_normal() * 10.0 ** rng.uniform(-6, 6))
+        sig = f(abs(rng.standard_normal()) * 10.0 ** rng.uniform(-6, 6))
+        s = f(np.float32(alpha) * alpha + sig)                 # fmaf(alpha, alpha, sig) up to 1 ulp
+        if not (1e-30 < s < 1e30):
+            continue
+        r = f(f(1.0 / np.sqrt(np.float64(s))) * f(1.0 + rng.uniform(-2, 2) * eps))
+        nrm = f(s * r)
+        b = -nrm if alpha >= 0 else nrm
+        rb = -r if alpha >= 0 else r
+        tau = f(f(b - alpha) * rb)
+        scale = f(1.0 / np.float64(f(alpha - b)))               # __frcp_rn: correctly rounded
+        s64 = np.float64(alpha) ** 2 + np.float64(sig)
+        bx = -np.sqrt(s64) if alpha >= 0 else np.sqrt(s64)
+        for got, want in ((b, bx), (tau, (bx - alpha) / bx), (scale, 1.0 / (alpha - bx))):
+            worst = max(worst, abs(float(got) - want) / abs(want))
+    assert worst <= 8 * eps, worst / eps
