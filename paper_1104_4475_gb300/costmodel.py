@@ -214,7 +214,7 @@ def train(X, y, steps=3000, lr=3e-3, seed=0, log_every=0, log=None):
 def pick(model, m, n, precisions=(0,)):
     """The candidate (nb, ib, tree, BS, precision) with the smallest predicted
     makespan for an m x n factorization (no timing); exhaustive timing
-    (:func:`collect`) stays the fallback and the judge of this choice."""
+    (:func:`collect`) stays the fallback and decides whether this choice was right."""
     cands = [c for c in configs_for(m, with_lp=True) if c[4] in precisions]
     X = np.stack([features(m, n, *c) for c in cands])
     return cands[int(np.argmin(model.predict_log_seconds(X)))]
